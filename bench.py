@@ -1,0 +1,348 @@
+"""Benchmark: effective field + LLG torque inside adaptive Dormand-Prince
+RK45 on the large ferromagnet workload (1024 x 1024 x 8 cells of 2x2x1 nm,
+demag + exchange + uniaxial anisotropy + interfacial DMI, tol 1e-5).
+
+One benchmark step is one DP45 attempt (six field evaluations, the error
+estimate read back, accept/reject).  The metric counts field evaluations:
+Mcell-evals/s = sum over evaluations of cells x sublattices / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torchrun), as
+the path does not shard a single grid; value = all ranks' cell-evals / max
+time.  `--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "field+torque Mcell-evals/s"
+BASELINE_METRIC = "field+torque Mcell-evals/s & served solves/s (p50/p99) vs plain path @ stated err"
+UNIT = "Mcell-evals/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def kernel_bytes(g, nk_avg):
+    """Algorithmic DRAM bytes per launch of each pass (per eval), see the design doc."""
+    nx, ny, nz = g["shape"]
+    n = nx * ny * nz
+    kxn = g["Px"] // 2 + 1
+    kyn = g["Py"] // 2 + 1
+    kzn = g["Pz"] // 2 + 1
+    spec = 3 * kxn * ny * nz * 8            # x-transformed spectrum, complex64
+    khat = kxn * kyn * kzn * 6 * 4          # kernel octant, float32
+    return {
+        "pass_a": 12 * n * (1 + nk_avg) + 12 * n + spec,   # read m, k_j; write stage; write spectrum
+        "pass_b": 2 * spec + khat,                          # spectrum in/out + kernel octant
+        "field": spec + 12 * n + 12 * n,                    # spectrum in, stage m in, k out
+    }
+
+
+def geometry(shape):
+    def nice(n):
+        if n == 1:
+            return 1
+        c = [p for p in (2 ** k for k in range(1, 14)) if p >= 2 * n - 1][:1]
+        c += [p for p in (3 * 2 ** k for k in range(1, 13)) if p >= 2 * n - 1][:1]
+        return min(c)
+    return {"shape": shape, "Px": nice(shape[0]), "Py": nice(shape[1]), "Pz": nice(shape[2])}
+
+
+def traffic_from_profile(kernel):
+    """ncu DRAM bytes per launch recorded for this kernel source, or None if
+    the source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+        src = os.path.join(ROOT, "paper_2411_18194_gb300", "csrc", rec["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return rec["dram_bytes_per_launch"] if sha == rec["source_sha"] else None
+    except Exception:
+        return None
+
+
+def cpu_baseline(seconds=15.0):
+    """The FP64 oracle (numpy, one thread) on a sub-grid of the same
+    workload: 128 x 128 x 8 cells, same materials and cell size."""
+    import numpy as np
+    from inputs import config_c2, random_unit_vectors
+    from oracle import dp45
+    w = config_c2()
+    p = w.problem
+    p.shape = (128, 128, 8)
+    p.regions = np.zeros((8, 128, 128), dtype=np.uint8)
+    m = random_unit_vectors(w.seed, p.shape).astype(np.float64)
+    o = dp45.Oracle(p)
+    st = dp45.State([m])
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.rhs(st)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds:
+            break
+    cells = 128 * 128 * 8
+    return {"value": n * cells / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d field+torque evaluations of a 128x128x8 sub-grid of the workload "
+                      "(same materials, cell size), FP64 numpy, %.1f s" % (n, el)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from inputs import config_c2, random_unit_vectors
+    from oracle import dp45
+    w = config_c2()
+    p = w.problem
+    p.shape = (128, 128, 8)
+    p.regions = np.zeros((8, 128, 128), dtype=np.uint8)
+    m = random_unit_vectors(w.seed, p.shape).astype(np.float64)
+    o = dp45.Oracle(p)
+    st = dp45.State([m])
+    k1 = o.rhs(st)
+    dt = 1e-14
+    for _ in range(args.warmup):
+        st2, _, _ = o.attempt(st, k1, dt)
+    e0 = o.evals
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st2, _, _ = o.attempt(st, k1, dt)
+    el = time.perf_counter() - t0
+    cells = 128 * 128 * 8
+    value = (o.evals - e0) * cells / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "baseline_metric": BASELINE_METRIC, "value": value,
+            "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random m0)",
+            "config": {"workload": "ferromagnet 1024x1024x8 (2x2x1 nm), demag+exchange+anisotropy+iDMI, "
+                                   "adaptive DP45 tol 1e-5; each step a bounded sample: one DP45 attempt "
+                                   "on a 128x128x8 sub-grid", "cells_per_step_eval": cells},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "DP45 attempts (6 evaluations each) on a 128x128x8 sub-grid, "
+                                       "FP64 numpy, one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2411_18194_gb300 as pkg
+    from inputs import config_c2
+    w = config_c2()
+    p = w.problem
+    nx, ny, nz = p.shape
+    ncell = nx * ny * nz * p.n_sub
+    mag = pkg.Magnet.from_problem(p)
+    m0 = torch.from_numpy(w.m0[0]).cuda()
+    mag.set_m(0, m0)
+    mag.set_solver(adaptive=True, dt=w.dt, tol=w.tol, dt_min=1e-18, dt_max=1e-11)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also builds the demag kernel spectrum)
+    for _ in range(args.warmup):
+        mag.step(1)
+    mag.profile(True)
+    clocks = ClockSampler(local)
+    barrier()
+    e0 = mag.time()["evals"]
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    attempts = 0
+    while attempts < args.steps:
+        mag.step(1)
+        attempts += 1
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(stop)
+    tinfo = mag.time()
+    evals = tinfo["evals"] - e0
+    prof = mag.profile_read()
+    mag.profile(False)
+    launches = sum(v[0] for v in prof.values())
+    t_rank = torch.tensor([ms], device="cuda")
+    ev_rank = torch.tensor([float(evals * ncell)], device="cuda")
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ev_rank, op=dist.ReduceOp.SUM)
+    t_max = t_rank.item()
+    value = ev_rank.item() / (t_max * 1e-3) / 1e6
+
+    # roofline of the dominant kernel
+    g = geometry(p.shape)
+    nk_avg = (0 + 1 + 2 + 3 + 4 + 5 + 5) / 7.0   # k vectors read by stage assembly per eval (a72 = 0)
+    kb = kernel_bytes(g, nk_avg)
+    dom = max((k for k in prof if k in kb), key=lambda k: prof[k][1])
+    n_l, tot_ms = prof[dom]
+    avg_s = tot_ms / n_l * 1e-3
+    peak, src = peaks()
+    achieved = kb[dom] / avg_s / 1e9
+    share = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
+
+    # end to end through the public API with host buffers: per step the state
+    # is copied in from pinned host memory and read back.
+    host_in = torch.from_numpy(w.m0[0]).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    mag.get_m(0, host_in)
+    e2e_steps = max(5, args.steps // 10)
+    barrier()
+    e1 = mag.time()["evals"]
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        mag.set_m(0, host_in)
+        mag.step(1)
+        mag.get_m(0, host_out)
+        host_in, host_out = host_out, host_in
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_evals = mag.time()["evals"] - e1
+    e2e_value = e2e_evals * ncell / e2e_s / 1e6
+    e2e_t = torch.tensor([e2e_value], device="cuda")
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.SUM)
+    nbytes = 12 * nx * ny * nz
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "baseline_metric": BASELINE_METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random m0)",
+            "config": {"workload": "ferromagnet 1024x1024x8 cells of 2x2x1 nm, Ms 1.1e6, A 1.6e-11, "
+                                   "Ku 8e5 (z), iDMI 3e-3, alpha 0.1; demag+exchange+anisotropy+iDMI; "
+                                   "adaptive DP45 tol 1e-5 from dt 1e-14",
+                       "cells": nx * ny * nz, "sublattices": p.n_sub, "parallelism": "replicas",
+                       "step": "one DP45 attempt (6 field evaluations + error readback)",
+                       "evals": evals, "accepted": tinfo["steps"], "rejected": tinfo["rejected"],
+                       "sim_time_s": tinfo["t"], "dt_s": tinfo["dt"],
+                       "l2": "inputs larger than L2 (state + stages + spectra ~1.3 GB)"},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic_from_profile(dom), "bytes_per_launch": kb[dom],
+                         "avg_launch_ms": avg_s * 1e3, "launches": n_l},
+            "kernel_share": share,
+            "cpu_baseline": cpu_baseline() if not args.no_cpu_baseline else None,
+            "e2e": {"value": e2e_t.item(), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    mag.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * mmp.h -- C-ABI of the GB300 micromagnetic field/torque library (libmmp.so).
+ *
+ * One context (`mmp_ctx`) holds one magnet on a regular grid of nx*ny*nz
+ * cuboid cells of size cx*cy*cz (metres) with one or two sublattices, its
+ * material parameters, its state and its solver.  This follows the problem
+ * statement of arXiv 2411.18194, Methods: the unit magnetisation of each
+ * magnet evolves as dm/dt = tau (Eq. magnetic-dynamic-equation), with the LLG torque of
+ * Eq. (LLG_torque), the effective-field terms listed after it (external,
+ * uniaxial anisotropy, exchange, demagnetising, DMI, magnetoelastic), the
+ * antiferromagnetic exchange of Eq. (AFM_exchange_field), the elastodynamics
+ * of Eq. (elasticity) and the embedded Runge-Kutta solvers of the solver
+ * table (Dormand-Prince RK45 here).
+ *
+ * Conventions shared by every call
+ *   - Units: SI.  Fields in tesla, magnetisation in A/m, time in seconds.
+ *   - Vector fields are SoA float32 [3][nz][ny][nx] (x fastest); cell index
+ *     c = x + nx*(y + ny*z).
+ *   - Pointers to vector fields may be host or device pointers (the library
+ *     copies with cudaMemcpyDefault on the context's stream).  The caller
+ *     owns every pointer it passes; the library owns everything it
+ *     allocates.  The library allocates device memory through the caller's
+ *     allocator when one is given at creation, else with cudaMalloc.
+ *   - All device work is enqueued on the context's stream.  Calls that
+ *     return host values, or read/write host buffers, synchronise that
+ *     stream before returning.
+ *   - Errors: a negative status; mmp_last_error() gives a message (thread
+ *     local).  After MMP_E_CUDA the context is poisoned and later calls
+ *     return MMP_E_STATE.  Unsupported requests fail with MMP_E_INVAL; the
+ *     library never falls back to another code path.
+ *   - One context must be used by one host thread at a time.
+ */
+#ifndef MMP_H
+#define MMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MMP_VERSION 1
+
+typedef struct mmp_ctx mmp_ctx;
+
+enum mmp_status {
+    MMP_OK = 0,
+    MMP_E_INVAL = -1,      /* bad argument or unsupported configuration */
+    MMP_E_OOM = -2,        /* device allocation failed */
+    MMP_E_CUDA = -3,       /* a CUDA call failed; the context is poisoned */
+    MMP_E_NONFINITE = -4,  /* a NaN/Inf appeared; the step was rolled back */
+    MMP_E_TIMEOUT = -5,    /* a host-side deadline passed */
+    MMP_E_STATE = -6       /* context poisoned or call out of order */
+};
+
+/* Per-sublattice, per-region scalar parameters (mmp_set_param). */
+enum mmp_param {
+    MMP_MS = 0,     /* saturation magnetisation Ms (A/m); Ms = 0 marks an empty cell */
+    MMP_AEX = 1,    /* ferromagnetic exchange stiffness A11 (J/m) */
+    MMP_ALPHA = 2,  /* Gilbert damping */
+    MMP_KU1 = 3,    /* first uniaxial anisotropy constant along ANIS_U (J/m^3) */
+    MMP_KU2 = 4,    /* second-order uniaxial constant along ANIS_U (J/m^3) */
+    MMP_KB1 = 5,    /* second uniaxial constant along ANIS_UB (J/m^3) */
+    MMP_DIND = 6,   /* interfacial DMI strength D (J/m^2) */
+    MMP_B1 = 7,     /* first magnetoelastic coupling constant (J/m^3) */
+    MMP_B2 = 8,     /* second magnetoelastic coupling constant (J/m^3) */
+    MMP_NPARAM = 9
+};
+
+/* Per-sublattice, per-region vector parameters (mmp_set_param3). */
+enum mmp_param3 {
+    MMP_ANIS_U = 0,   /* uniaxial axis of KU1/KU2 (normalised by the library) */
+    MMP_ANIS_UB = 1,  /* uniaxial axis of KB1 (normalised by the library) */
+    MMP_B_EXT = 2,    /* external field (T) */
+    MMP_NPARAM3 = 3
+};
+
+/* Global constants (mmp_set_global). */
+enum mmp_global {
+    MMP_A0 = 0,         /* homogeneous AFM exchange A0 (J/m), Eq. AFM_exchange_field */
+    MMP_A12 = 1,        /* inhomogeneous AFM exchange A12 (J/m) */
+    MMP_LATTICE_A = 2,  /* lattice parameter a (m) */
+    MMP_C11 = 3,        /* cubic stiffness c11 (Pa) */
+    MMP_C12 = 4,        /* cubic stiffness c12 (Pa) */
+    MMP_C44 = 5,        /* cubic stiffness c44 (Pa) */
+    MMP_RHO = 6,        /* mass density (kg/m^3) */
+    MMP_ETA = 7,        /* viscous (Rayleigh stiffness) damping time (s) */
+    MMP_NGLOBAL = 8
+};
+
+/* Field terms (mmp_enable_terms bitmask). */
+enum mmp_term {
+    MMP_T_DEMAG = 1,     /* FFT demag of M = sum_s Ms m (Methods, Magnetostatic field) */
+    MMP_T_EXCH = 2,      /* 6-neighbour exchange (first term of Eq. AFM_exchange_field) */
+    MMP_T_ANIS = 4,      /* uniaxial anisotropy (KU1, KU2 along ANIS_U; KB1 along ANIS_UB) */
+    MMP_T_DMI = 8,       /* interfacial DMI (Eq. dmi, interfacial tensor) + Neumann BC */
+    MMP_T_ZEEMAN = 16,   /* external field B_EXT */
+    MMP_T_AFM = 32,      /* A12 and A0 terms of Eq. AFM_exchange_field (2 sublattices) */
+    MMP_T_MEL = 64,      /* magnetoelastic field/force (Eqs. magnetoelastic-field/-force) */
+    MMP_T_ELASTIC = 128  /* elastodynamics rho u'' = f_tot (Eq. elasticity) */
+};
+
+enum mmp_method { MMP_DP45 = 0 };
+
+typedef void* (*mmp_alloc_fn)(size_t bytes, void* user);
+typedef void (*mmp_free_fn)(void* ptr, void* user);
+
+/* Create a context.  nx, ny, nz >= 1 (padded FFT lengths are at most 4096
+ * per axis; nz <= 16 when the demag term is on); cx, cy, cz > 0 (m);
+ * n_sublattices 1 or 2; `stream` is a cudaStream_t (NULL = legacy default
+ * stream); `alloc`/`dealloc`/`user` an optional device allocator (both or
+ * neither).  On success *out owns the context.  Errors: MMP_E_INVAL,
+ * MMP_E_OOM, MMP_E_CUDA (e.g. no GPU). */
+int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, double cz,
+               int n_sublattices, void* stream, mmp_alloc_fn alloc, mmp_free_fn dealloc,
+               void* user);
+
+/* Destroy a context and free everything it allocated (NULL is allowed). */
+int mmp_destroy(mmp_ctx* ctx);
+
+/* Region map: nx*ny*nz uint8 (host or device pointer), region r selects
+ * row r of every parameter table.  Default: all cells in region 0. */
+int mmp_set_region_map(mmp_ctx* ctx, const uint8_t* regions);
+
+/* Set a scalar (mmp_set_param) or vector (mmp_set_param3) parameter of
+ * sublattice `sub` (-1 = all) in `region` (0..255, -1 = all). */
+int mmp_set_param(mmp_ctx* ctx, int sub, int param, int region, double value);
+int mmp_set_param3(mmp_ctx* ctx, int sub, int param, int region, double x, double y, double z);
+int mmp_set_global(mmp_ctx* ctx, int param, double value);
+
+/* Select the field terms (bitmask of mmp_term).  Two-sublattice contexts
+ * with DMI, and the elastic/magnetoelastic terms with empty cells, are
+ * rejected (MMP_E_INVAL at the next evaluation). */
+int mmp_enable_terms(mmp_ctx* ctx, unsigned terms);
+
+/* State.  m: [3][nz][ny][nx] float32 of sublattice `sub`; with normalize != 0
+ * each vector is scaled to unit length on the device.  u, v: elastic
+ * displacement (m) and velocity (m/s), same layout.  Setting the state
+ * invalidates the cached first Runge-Kutta stage. */
+int mmp_set_m(mmp_ctx* ctx, int sub, const float* m, int normalize);
+int mmp_get_m(mmp_ctx* ctx, int sub, float* m);
+int mmp_set_elastic(mmp_ctx* ctx, const float* u, const float* v);
+int mmp_get_elastic(mmp_ctx* ctx, float* u, float* v);
+
+/* Solver.  method = MMP_DP45.  adaptive = 0: fixed step dt.  adaptive = 1:
+ * dt is the initial step, tol the absolute max-norm tolerance on the error
+ * estimate dt*max|sum_i (b_i - b*_i) k_i| of m, dt in [dt_min, dt_max]. */
+int mmp_set_solver(mmp_ctx* ctx, int method, int adaptive, double dt, double tol,
+                   double dt_min, double dt_max);
+
+/* Evaluate B_eff and the LLG torque of sublattice `sub` at the current state
+ * (one field evaluation).  B (T) and tau = dm/dt (1/s) are
+ * [3][nz][ny][nx] float32, host or device, either may be NULL. */
+int mmp_eval_field(mmp_ctx* ctx, int sub, float* B, float* tau);
+
+/* Advance nsteps DP45 steps (fixed or adaptive; an adaptive step reads the
+ * 4-byte error estimate back once per attempt).  Returns MMP_E_NONFINITE
+ * (state rolled back to the last accepted step) if the error is NaN/Inf. */
+int mmp_step(mmp_ctx* ctx, int nsteps);
+
+/* Advance by `duration` seconds (the last step is shortened to land on time). */
+int mmp_run(mmp_ctx* ctx, double duration);
+
+/* Relax: damping-only torque -gamma alpha/(1+alpha^2) m x (m x B), adaptive
+ * DP45, until max|m x B| <= torque_tol_T (tesla), or simulated time
+ * max_time, or host wall time timeout_s (then MMP_E_TIMEOUT). */
+int mmp_relax(mmp_ctx* ctx, double torque_tol_T, double max_time, double timeout_s);
+
+/* Time, step size and counters (field evaluations, accepted and rejected
+ * steps) since creation. */
+int mmp_get_time(mmp_ctx* ctx, double* t, double* dt, long long* steps,
+                 long long* rejected, long long* evals);
+
+/* Checkpoint: serialise (size query with blob = NULL) / restore the state
+ * (m of every sublattice, u, v, t, dt, counters) to/from a host blob.  A
+ * restored run continues bitwise identically on the same device. */
+int mmp_get_state(mmp_ctx* ctx, void* blob, size_t* size);
+int mmp_set_state(mmp_ctx* ctx, const void* blob, size_t size);
+
+/* Tracing: with enable != 0, every kernel launch of the context is bracketed
+ * by CUDA events on the context's stream (counters reset); enable = 0 stops
+ * recording.  mmp_profile_read synchronises the stream and returns, for
+ * kernel `kernel` (an mmp_kernel), the number of launches and their summed
+ * device time since the last reset. */
+enum mmp_kernel {
+    MMP_K_PASS_A = 0,     /* stage assembly + forward x FFT */
+    MMP_K_PASS_B = 1,     /* y FFT, z transform, kernel multiply, inverse y/z */
+    MMP_K_FIELD = 2,      /* inverse x FFT + local field + LLG torque (+ error) */
+    MMP_K_ASSEMBLE = 3,   /* stage assembly without demag */
+    MMP_K_STRAIN = 4,     /* strain and stress */
+    MMP_K_ELASTIC = 5,    /* elastic + magnetoelastic force */
+    MMP_NKERNEL = 6
+};
+int mmp_profile(mmp_ctx* ctx, int enable);
+int mmp_profile_read(mmp_ctx* ctx, int kernel, long long* launches, double* total_ms);
+
+/* Wait for all work of the context. */
+int mmp_sync(mmp_ctx* ctx);
+
+/* Message of the last error on this thread ("" if none). */
+const char* mmp_last_error(void);
+
+/* MMP_VERSION of the library. */
+int mmp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMP_H */

@@ -1,0 +1,295 @@
+"""ctypes binding of libmmp.so (include/mmp.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device memory comes from PyTorch's caching allocator (passed to
+mmp_create as the context allocator) and work is enqueued on the current
+PyTorch CUDA stream unless another stream is given.  If the library is
+missing the import-time lookup fails loudly; there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libmmp.so")
+
+TERM_BITS = {"DEMAG": 1, "EXCH": 2, "ANIS": 4, "DMI": 8, "ZEEMAN": 16, "AFM": 32, "MEL": 64,
+             "ELASTIC": 128}
+PARAM_IDS = {"MS": 0, "AEX": 1, "ALPHA": 2, "KU1": 3, "KU2": 4, "KB1": 5, "DIND": 6, "B1": 7, "B2": 8}
+PARAM3_IDS = {"ANIS_U": 0, "ANIS_UB": 1, "B_EXT": 2}
+GLOBAL_IDS = {"A0": 0, "A12": 1, "LATTICE_A": 2, "C11": 3, "C12": 4, "C44": 5, "RHO": 6, "ETA": 7}
+STATUS = {0: "MMP_OK", -1: "MMP_E_INVAL", -2: "MMP_E_OOM", -3: "MMP_E_CUDA", -4: "MMP_E_NONFINITE",
+          -5: "MMP_E_TIMEOUT", -6: "MMP_E_STATE"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_c = ctypes
+_SIGS = {
+    "mmp_version": ([], _c.c_int),
+    "mmp_last_error": ([], _c.c_char_p),
+    "mmp_create": ([_c.POINTER(_c.c_void_p), _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double,
+                    _c.c_double, _c.c_int, _c.c_void_p, ALLOC_FN, FREE_FN, _c.c_void_p], _c.c_int),
+    "mmp_destroy": ([_c.c_void_p], _c.c_int),
+    "mmp_set_region_map": ([_c.c_void_p, _c.c_void_p], _c.c_int),
+    "mmp_set_param": ([_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_double], _c.c_int),
+    "mmp_set_param3": ([_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double,
+                        _c.c_double], _c.c_int),
+    "mmp_set_global": ([_c.c_void_p, _c.c_int, _c.c_double], _c.c_int),
+    "mmp_enable_terms": ([_c.c_void_p, _c.c_uint], _c.c_int),
+    "mmp_set_m": ([_c.c_void_p, _c.c_int, _c.c_void_p, _c.c_int], _c.c_int),
+    "mmp_get_m": ([_c.c_void_p, _c.c_int, _c.c_void_p], _c.c_int),
+    "mmp_set_elastic": ([_c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "mmp_get_elastic": ([_c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "mmp_set_solver": ([_c.c_void_p, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double,
+                        _c.c_double], _c.c_int),
+    "mmp_eval_field": ([_c.c_void_p, _c.c_int, _c.c_void_p, _c.c_void_p], _c.c_int),
+    "mmp_step": ([_c.c_void_p, _c.c_int], _c.c_int),
+    "mmp_run": ([_c.c_void_p, _c.c_double], _c.c_int),
+    "mmp_relax": ([_c.c_void_p, _c.c_double, _c.c_double, _c.c_double], _c.c_int),
+    "mmp_get_time": ([_c.c_void_p, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double),
+                      _c.POINTER(_c.c_longlong), _c.POINTER(_c.c_longlong), _c.POINTER(_c.c_longlong)],
+                     _c.c_int),
+    "mmp_get_state": ([_c.c_void_p, _c.c_void_p, _c.POINTER(_c.c_size_t)], _c.c_int),
+    "mmp_set_state": ([_c.c_void_p, _c.c_void_p, _c.c_size_t], _c.c_int),
+    "mmp_sync": ([_c.c_void_p], _c.c_int),
+    "mmp_profile": ([_c.c_void_p, _c.c_int], _c.c_int),
+    "mmp_profile_read": ([_c.c_void_p, _c.c_int, _c.POINTER(_c.c_longlong), _c.POINTER(_c.c_double)],
+                         _c.c_int),
+}
+KERNEL_IDS = {"pass_a": 0, "pass_b": 1, "field": 2, "assemble": 3, "strain": 4, "elastic": 5}
+
+_lib = None
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def library():
+    """The loaded libmmp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libmmp.so not found at %s: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % _LIB_PATH)
+        lib = ctypes.CDLL(_LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+class MmpError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, message))
+        self.status = status
+
+
+def _check(status):
+    if status != 0:
+        raise MmpError(status, library().mmp_last_error().decode(errors="replace"))
+    return status
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor (device or host) or a numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be C-contiguous")
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return a.data_ptr()
+
+
+class _TorchAllocator:
+    """Device allocations of the library served by PyTorch's caching allocator."""
+
+    def __init__(self, device, stream):
+        import torch
+        self._torch = torch
+        self._device = device
+        self._stream = stream
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), self._device, self._stream)
+        except Exception:
+            return None
+
+    def _free(self, ptr, user):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+
+class Magnet:
+    """One magnet on a regular grid (an mmp_ctx).
+
+    Vector fields are float32 [3][nz][ny][nx]; methods accept torch tensors
+    (device or host) or C-contiguous numpy arrays.
+    """
+
+    def __init__(self, shape, cell, n_sub=1, stream=None, torch_allocator=True):
+        lib = library()
+        nx, ny, nz = (int(v) for v in shape)
+        self.shape = (nx, ny, nz)
+        self.cell = tuple(float(c) for c in cell)
+        self.n_sub = int(n_sub)
+        self._alloc = None
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        alloc_fn, free_fn = ALLOC_FN(), FREE_FN()
+        if torch_allocator:
+            self._alloc = _TorchAllocator(torch.cuda.current_device(), stream)
+            alloc_fn, free_fn = self._alloc.alloc, self._alloc.free
+        ctx = ctypes.c_void_p()
+        _check(lib.mmp_create(ctypes.byref(ctx), nx, ny, nz, *self.cell, self.n_sub,
+                              ctypes.c_void_p(handle), alloc_fn, free_fn, None))
+        self._ctx = ctx
+
+    # ------------------------------------------------------------ lifetime --
+    def close(self):
+        if getattr(self, "_ctx", None):
+            library().mmp_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------- parameters --
+    def set_region_map(self, regions):
+        regions = np.ascontiguousarray(regions, dtype=np.uint8) if isinstance(regions, np.ndarray) else regions
+        _check(library().mmp_set_region_map(self._ctx, _ptr(regions)))
+
+    def set_param(self, name, value, sub=-1, region=-1):
+        _check(library().mmp_set_param(self._ctx, sub, PARAM_IDS[name], region, float(value)))
+
+    def set_param3(self, name, vec, sub=-1, region=-1):
+        x, y, z = (float(v) for v in vec)
+        _check(library().mmp_set_param3(self._ctx, sub, PARAM3_IDS[name], region, x, y, z))
+
+    def set_global(self, name, value):
+        _check(library().mmp_set_global(self._ctx, GLOBAL_IDS[name], float(value)))
+
+    def enable_terms(self, terms):
+        mask = terms if isinstance(terms, int) else sum(TERM_BITS[t] for t in terms)
+        _check(library().mmp_enable_terms(self._ctx, mask))
+
+    # --------------------------------------------------------------- state --
+    def set_m(self, sub, m, normalize=False):
+        _check(library().mmp_set_m(self._ctx, sub, _ptr(m), int(bool(normalize))))
+
+    def get_m(self, sub, out):
+        _check(library().mmp_get_m(self._ctx, sub, _ptr(out)))
+        return out
+
+    def set_elastic(self, u=None, v=None):
+        _check(library().mmp_set_elastic(self._ctx, _ptr(u), _ptr(v)))
+
+    def get_elastic(self, u=None, v=None):
+        _check(library().mmp_get_elastic(self._ctx, _ptr(u), _ptr(v)))
+        return u, v
+
+    # -------------------------------------------------------------- solver --
+    def set_solver(self, adaptive=False, dt=1e-13, tol=1e-5, dt_min=1e-18, dt_max=1e-11):
+        _check(library().mmp_set_solver(self._ctx, 0, int(bool(adaptive)), dt, tol, dt_min, dt_max))
+
+    def eval_field(self, sub=0, B=None, tau=None):
+        _check(library().mmp_eval_field(self._ctx, sub, _ptr(B), _ptr(tau)))
+        return B, tau
+
+    def step(self, nsteps=1):
+        _check(library().mmp_step(self._ctx, int(nsteps)))
+
+    def run(self, duration):
+        _check(library().mmp_run(self._ctx, float(duration)))
+
+    def relax(self, torque_tol=1e-4, max_time=10e-9, timeout_s=0.0):
+        _check(library().mmp_relax(self._ctx, float(torque_tol), float(max_time), float(timeout_s)))
+
+    def time(self):
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        s, r, e = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(library().mmp_get_time(self._ctx, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(s),
+                                      ctypes.byref(r), ctypes.byref(e)))
+        return dict(t=t.value, dt=dt.value, steps=s.value, rejected=r.value, evals=e.value)
+
+    def get_state(self):
+        size = ctypes.c_size_t()
+        _check(library().mmp_get_state(self._ctx, None, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        _check(library().mmp_get_state(self._ctx, buf, ctypes.byref(size)))
+        return bytes(buf.raw[:size.value])
+
+    def set_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(library().mmp_set_state(self._ctx, buf, len(blob)))
+
+    def sync(self):
+        _check(library().mmp_sync(self._ctx))
+
+    def profile(self, enable=True):
+        """Start (reset) or stop per-kernel CUDA-event timing."""
+        _check(library().mmp_profile(self._ctx, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel: (launches, total device ms)} since the last reset."""
+        out = {}
+        for name, k in KERNEL_IDS.items():
+            n, ms = ctypes.c_longlong(), ctypes.c_double()
+            _check(library().mmp_profile_read(self._ctx, k, ctypes.byref(n), ctypes.byref(ms)))
+            if n.value:
+                out[name] = (n.value, ms.value)
+        return out
+
+    # ------------------------------------------------------------ helpers --
+    @classmethod
+    def from_problem(cls, problem, **kw):
+        """A context set up from an object with the attributes of
+        inputs.Problem (shape, cell, n_sub, regions, scal, vec, glob, terms)."""
+        mag = cls(problem.shape, problem.cell, problem.n_sub, **kw)
+        regions = np.ascontiguousarray(problem.regions, dtype=np.uint8)
+        used = np.unique(regions)
+        if used.size > 1 or used[0] != 0:
+            mag.set_region_map(regions)
+        for name in PARAM_IDS:
+            table = problem.scal[name]
+            for s in range(problem.n_sub):
+                vals = table[s, used]
+                if np.all(vals == vals[0]):
+                    mag.set_param(name, vals[0], s, -1)
+                else:
+                    for r in used:
+                        mag.set_param(name, table[s, r], s, int(r))
+        for name in PARAM3_IDS:
+            table = problem.vec[name]
+            for s in range(problem.n_sub):
+                vals = table[s, used]
+                if np.all(vals == vals[0]):
+                    mag.set_param3(name, vals[0], s, -1)
+                else:
+                    for r in used:
+                        mag.set_param3(name, table[s, r], s, int(r))
+        for name in GLOBAL_IDS:
+            mag.set_global(name, problem.glob.get(name, 0.0))
+        mag.enable_terms(sorted(problem.terms))
+        return mag

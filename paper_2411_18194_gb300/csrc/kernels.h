@@ -1,0 +1,105 @@
+// kernels.h -- launch interface between the C-ABI layer (mmp.cu) and the
+// device passes (passes.cu, tensor.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace mmp {
+
+// ---------------------------------------------------------------- tensor --
+struct KernelBuild {
+  int n[3];            // grid extents
+  int P[3];            // padded lengths
+  double cell[3];      // cell size (m)
+  double rc;           // Newell/asymptotic cutoff in units of max(cell)
+  double* buf0;        // FP64 scratch, 6 * max(extent products) doubles
+  double* buf1;
+  const double2* trig[3];   // (cos, sin)(2 pi t / P_a), device
+  float* out;          // [Px/2+1][Py/2+1][Pz/2+1][6]
+};
+cudaError_t build_kernel_spectrum(const KernelBuild& kb, cudaStream_t s);
+
+// ------------------------------------------------------------ geometry ---
+struct Grid {
+  int nx, ny, nz;
+  long long n;          // nx*ny*nz
+  int Px, Py, Pz;       // padded lengths (1 on axes with n = 1)
+  int kxn;              // Px/2 + 1
+  int kyn, kzn;         // Py/2 + 1, Pz/2 + 1
+  float h[3];           // cell size (m)
+  float ih[3];          // 1 / h
+};
+
+// State layout: one float vector per RK quantity,
+//   [sub 0: m (3n)] [sub 1: m (3n)] [u (3n)] [v (3n)]   (u, v with elastic)
+struct StageArgs {
+  const float* y;            // state at the start of the step
+  const float* k[7];         // previous stages (nk used)
+  float coef[7];             // dt * a_ij (rounded from FP64)
+  int nk;
+  int normalize;             // renormalise m (the 5th-order stage)
+  float* stage;              // output stage state
+  int nparts;                // 3-vectors in the state (nsub, + 2 with elastic)
+  int nsub;
+};
+
+struct DemagArgs {
+  float2* T;                 // spectrum [kxn][3][nz][ny] complex
+  const float* khat;         // kernel octant [kxn][kyn][kzn][6]
+  const float2* tw_x;        // Px roots (forward)
+  const float2* tw_y;        // Py roots
+  const float2* tw_ly;       // Ly = Py / R roots
+  const float2* tw_z;        // Pz roots
+  FftPlan plan_x, plan_ly;
+  int R;                     // residue classes of ky per cluster
+};
+
+struct Coefs {
+  const RegionCoef* reg;     // [nsub][256]
+  const uint8_t* regions;    // [n] or null when uniform
+  const float2* hA;          // harmonic-mean A pair table [nsub][256][256] (multi-region)
+  int uniform;
+};
+
+struct FieldArgs {
+  const float* stage;        // stage state
+  float* kout;               // output derivative (same layout as the state)
+  float* Bout;               // optional B_eff [nsub][3][n]
+  const float* eps;          // strain [6][n] (magnetoelastic)
+  unsigned terms;
+  // error estimate of the 5th-order stage: err = max |sum_j e_j k_j|
+  const float* ek[6];
+  float ecoef[7];            // dt * (b_j - b*_j)
+  unsigned* err;             // atomicMax target (float bits)
+  int relax;                 // damping-only torque (relax mode)
+  unsigned* torque_max;      // max |m x B| (float bits) in relax mode
+};
+
+struct ElasticArgs {
+  const float* stage;        // stage state (u, v at parts nsub, nsub+1)
+  float* kout;
+  float* eps;                // [6][n] strain out
+  float* sig;                // [6][n] stress out
+  float c11, c12, c44, eta, inv_rho;
+  unsigned terms;
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_assemble(const Grid& g, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_passA(const Grid& g, const StageArgs& a, const DemagArgs& d, const Coefs& c,
+                         int threads, cudaStream_t s);
+cudaError_t launch_passB(const Grid& g, const DemagArgs& d, int threads, cudaStream_t s);
+cudaError_t launch_field(const Grid& g, const DemagArgs& d, const Coefs& c, const FieldArgs& f,
+                         int nsub, bool demag, int threads, cudaStream_t s);
+cudaError_t launch_strain(const Grid& g, const ElasticArgs& e, int nsub, cudaStream_t s);
+cudaError_t launch_elastic_rhs(const Grid& g, const ElasticArgs& e, const Coefs& c, int nsub,
+                               cudaStream_t s);
+cudaError_t launch_normalize(float* m, long long n, cudaStream_t s);
+
+// shared memory bytes of each pass (host side planning)
+size_t smem_passA(const Grid& g);
+size_t smem_passB(const Grid& g, int R);
+size_t smem_field(const Grid& g, bool demag);
+
+}  // namespace mmp

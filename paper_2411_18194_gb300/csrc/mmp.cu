@@ -1,0 +1,970 @@
+// mmp.cu -- the C-ABI (include/mmp.h): context, parameters, set-up of the
+// demag kernel spectrum, evaluation sequencing and the Dormand-Prince RK45
+// controller (FP64 time, step size and error control on the host).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kernels.h"
+#include "mmp.h"
+
+using namespace mmp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+// Dormand and Prince (1980) RK5(4)7FM tableau, FSAL, local extrapolation.
+const double kA[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+const double kB4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100,
+                       1.0 / 40};
+// step-size controller (a reading of what the paper leaves open)
+const double kSafety = 0.9, kGrowMin = 0.2, kGrowMax = 5.0, kExponent = 0.2;
+const double kRc = 10.0;   // Newell below 10 max(cell), asymptotic above
+
+int nice_length(int n) {
+  // smallest even 2^a or 3*2^a >= 2n - 1 (1 when n == 1)
+  if (n == 1) return 1;
+  int best = 1 << 30;
+  for (int p = 2; p < (1 << 30); p *= 2)
+    if (p >= 2 * n - 1) { best = std::min(best, p); break; }
+  for (int p = 6; p < (1 << 30); p *= 2)
+    if (p >= 2 * n - 1) { best = std::min(best, p); break; }
+  return best;
+}
+
+bool make_plan(int L, FftPlan& p) {
+  p.L = L;
+  p.n16 = p.n8 = p.n4 = p.n2 = p.n3 = 0;
+  int r = L, a = 0;
+  while (r % 3 == 0) { r /= 3; p.n3++; }
+  while (r % 2 == 0) { r /= 2; a++; }
+  if (r != 1) return false;
+  p.n16 = a / 4;
+  p.n8 = (a % 4) == 3;
+  p.n4 = (a % 4) == 2;
+  p.n2 = (a % 4) == 1;
+  return true;
+}
+
+std::vector<float2> roots(int P) {
+  std::vector<float2> w(P);
+  for (int t = 0; t < P; ++t) {
+    double a = 2.0 * 3.14159265358979323846 * (double)t / (double)P;
+    w[t] = make_float2((float)cos(a), (float)(-sin(a)));
+  }
+  return w;
+}
+
+float2 split(double v) {
+  float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+}  // namespace
+
+struct mmp_ctx {
+  Grid g;
+  int nsub = 1;
+  double cell[3];
+  cudaStream_t stream = nullptr;
+  mmp_alloc_fn ualloc = nullptr;
+  mmp_free_fn ufree = nullptr;
+  void* uuser = nullptr;
+  bool poisoned = false;
+  unsigned terms = 0;
+  // parameter tables (FP64)
+  double scal[MMP_NPARAM][2][MMP_MAX_REGIONS];
+  double vec[MMP_NPARAM3][2][MMP_MAX_REGIONS][3];
+  double glob[MMP_NGLOBAL];
+  bool uniform = true;
+  bool used[MMP_MAX_REGIONS] = {true};   // regions present in the map
+  bool coef_dirty = true, khat_dirty = true;
+  // device buffers
+  uint8_t* d_regions = nullptr;
+  RegionCoef* d_coef = nullptr;
+  float2* d_hA = nullptr;
+  float* d_y = nullptr;
+  float* d_stage = nullptr;
+  float* d_k[7] = {};
+  float* d_B = nullptr;
+  float* d_eps = nullptr;
+  float* d_sig = nullptr;
+  float2* d_T = nullptr;
+  float* d_khat = nullptr;
+  float2 *d_tw_x = nullptr, *d_tw_y = nullptr, *d_tw_ly = nullptr, *d_tw_z = nullptr;
+  unsigned* d_red = nullptr;   // [0] error bits, [1] torque bits
+  unsigned* h_red = nullptr;   // pinned
+  int nparts = 0;              // 3-vectors in the state
+  long long nstate = 0;        // floats in the state
+  FftPlan plan_x{}, plan_ly{};
+  int R = 1, thrA = 256, thrB = 256, thrC = 256;
+  // solver
+  int adaptive = 0;
+  double dt = 1e-13, tol = 1e-5, dt_min = 1e-18, dt_max = 1e-11;
+  double t = 0.0;
+  long long steps = 0, rejected = 0, evals = 0;
+  bool k1_valid = false;
+  int k1_relax = 0;
+  // tracing
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[MMP_NKERNEL];
+  size_t prof_used[MMP_NKERNEL] = {};
+};
+
+namespace {
+
+void* dalloc(mmp_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (c->ualloc) {
+    p = c->ualloc(bytes, c->uuser);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void dfree(mmp_ctx* c, void* p) {
+  if (!p) return;
+  if (c->ufree) c->ufree(p, c->uuser);
+  else cudaFree(p);
+}
+
+template <typename T>
+int alloc_into(mmp_ctx* c, T*& p, size_t bytes) {
+  dfree(c, p);
+  p = static_cast<T*>(dalloc(c, bytes));
+  if (!p) return fail(MMP_E_OOM, "device allocation of %zu bytes failed", bytes);
+  return MMP_OK;
+}
+
+int cuda_check(mmp_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MMP_OK;
+  c->poisoned = true;
+  return fail(MMP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                   \
+  do {                                                   \
+    int _rc = cuda_check(ctx, (expr), what);             \
+    if (_rc != MMP_OK) return _rc;                       \
+  } while (0)
+#define TRY(expr)                                        \
+  do {                                                   \
+    int _rc = (expr);                                    \
+    if (_rc != MMP_OK) return _rc;                       \
+  } while (0)
+
+int check_ctx(mmp_ctx* ctx) {
+  if (!ctx) return fail(MMP_E_INVAL, "null context");
+  if (ctx->poisoned) return fail(MMP_E_STATE, "context poisoned by an earlier CUDA error");
+  return MMP_OK;
+}
+
+bool has(const mmp_ctx* c, unsigned t) { return (c->terms & t) != 0; }
+
+int wanted_parts(const mmp_ctx* c) { return c->nsub + (has(c, MMP_T_ELASTIC) ? 2 : 0); }
+
+// (Re)allocate the state-sized buffers when the number of parts changes,
+// keeping the magnetisation (and u, v when they exist in both layouts).
+int ensure_state(mmp_ctx* ctx) {
+  int want = wanted_parts(ctx);
+  if (want == ctx->nparts && ctx->d_y) return MMP_OK;
+  long long n = ctx->g.n;
+  long long nstate = 3LL * want * n;
+  float* ny = static_cast<float*>(dalloc(ctx, nstate * sizeof(float)));
+  if (!ny) return fail(MMP_E_OOM, "state allocation failed");
+  CK(cudaMemsetAsync(ny, 0, nstate * sizeof(float), ctx->stream), "memset state");
+  if (ctx->d_y) {
+    int keep = std::min(ctx->nparts, want);
+    CK(cudaMemcpyAsync(ny, ctx->d_y, 3LL * keep * n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream),
+       "copy state");
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  dfree(ctx, ctx->d_y);
+  ctx->d_y = ny;
+  ctx->nparts = want;
+  ctx->nstate = nstate;
+  TRY(alloc_into(ctx, ctx->d_stage, nstate * sizeof(float)));
+  for (int i = 0; i < 7; ++i) TRY(alloc_into(ctx, ctx->d_k[i], nstate * sizeof(float)));
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+int upload_coefs(mmp_ctx* ctx) {
+  if (!ctx->coef_dirty) return MMP_OK;
+  std::vector<RegionCoef> rc(2 * MMP_MAX_REGIONS);
+  const double* h = ctx->cell;
+  const double A0 = ctx->glob[MMP_A0], A12 = ctx->glob[MMP_A12], alat = ctx->glob[MMP_LATTICE_A];
+  for (int s = 0; s < 2; ++s)
+    for (int r = 0; r < MMP_MAX_REGIONS; ++r) {
+      RegionCoef& c = rc[s * MMP_MAX_REGIONS + r];
+      memset(&c, 0, sizeof c);
+      if (s >= ctx->nsub) continue;
+      double Ms = ctx->scal[MMP_MS][s][r], A = ctx->scal[MMP_AEX][s][r], al = ctx->scal[MMP_ALPHA][s][r];
+      double D = ctx->scal[MMP_DIND][s][r];
+      c.ms = (float)Ms;
+      c.alpha = (float)al;
+      c.tq = (float)(-kGamma / (1.0 + al * al));
+      c.aex = (float)A;
+      c.dind = (float)D;
+      if (Ms <= 0.0) { c.ms = 0.0f; continue; }
+      double im = 1.0 / Ms;
+      c.inv_ms = (float)im;
+      for (int a = 0; a < 3; ++a) {
+        c.exch[a] = split(2.0 * A * im / (h[a] * h[a]));
+        c.two_over_ms_h2[a] = (float)(2.0 * im / (h[a] * h[a]));
+        c.two_over_ms_h2_df[a] = split(2.0 * im / (h[a] * h[a]));
+        c.dmi[a] = (float)(D * im / h[a]);
+        c.ghost[a] = A > 0 ? (float)(h[a] * D / (2.0 * A)) : 0.0f;
+        c.exbc[a] = A > 0 ? (float)(D * im / h[a]) : 0.0f;
+        c.afm12[a] = (float)(A12 * im / (h[a] * h[a]));
+      }
+      c.ku1 = (float)(2.0 * ctx->scal[MMP_KU1][s][r] * im);
+      c.ku2 = (float)(4.0 * ctx->scal[MMP_KU2][s][r] * im);
+      c.kb1 = (float)(2.0 * ctx->scal[MMP_KB1][s][r] * im);
+      const double* u = ctx->vec[MMP_ANIS_U][s][r];
+      const double* ub = ctx->vec[MMP_ANIS_UB][s][r];
+      double nu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      double nub = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+      for (int i = 0; i < 3; ++i) {
+        c.u[i] = nu > 0 ? (float)(u[i] / nu) : 0.0f;
+        c.ub[i] = nub > 0 ? (float)(ub[i] / nub) : 0.0f;
+        c.bext[i] = (float)ctx->vec[MMP_B_EXT][s][r][i];
+      }
+      c.afm0 = alat > 0 ? split(4.0 * A0 * im / (alat * alat)) : make_float2(0.0f, 0.0f);
+      c.mel1 = (float)(-2.0 * ctx->scal[MMP_B1][s][r] * im);
+      c.mel2 = (float)(-2.0 * ctx->scal[MMP_B2][s][r] * im);
+      c.b1 = (float)ctx->scal[MMP_B1][s][r];
+      c.b2 = (float)ctx->scal[MMP_B2][s][r];
+    }
+  CK(cudaMemcpyAsync(ctx->d_coef, rc.data(), rc.size() * sizeof(RegionCoef), cudaMemcpyHostToDevice,
+                     ctx->stream),
+     "upload coefficients");
+  if (!ctx->uniform) {
+    if (!ctx->d_hA) TRY(alloc_into(ctx, ctx->d_hA, (size_t)2 * MMP_MAX_REGIONS * MMP_MAX_REGIONS * sizeof(float2)));
+    std::vector<float2> hA((size_t)2 * MMP_MAX_REGIONS * MMP_MAX_REGIONS);
+    for (int s = 0; s < 2; ++s)
+      for (int a = 0; a < MMP_MAX_REGIONS; ++a)
+        for (int b = 0; b < MMP_MAX_REGIONS; ++b) {
+          double A1 = s < ctx->nsub ? ctx->scal[MMP_AEX][s][a] : 0.0;
+          double A2 = s < ctx->nsub ? ctx->scal[MMP_AEX][s][b] : 0.0;
+          double hm = (A1 + A2) != 0.0 ? 2.0 * A1 * A2 / (A1 + A2) : 0.0;
+          hA[((size_t)s * MMP_MAX_REGIONS + a) * MMP_MAX_REGIONS + b] = split(hm);
+        }
+    CK(cudaMemcpyAsync(ctx->d_hA, hA.data(), hA.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream),
+       "upload hA");
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->coef_dirty = false;
+  return MMP_OK;
+}
+
+int build_khat(mmp_ctx* ctx) {
+  if (!ctx->khat_dirty) return MMP_OK;
+  const Grid& g = ctx->g;
+  size_t nk = (size_t)g.kxn * g.kyn * g.kzn;
+  TRY(alloc_into(ctx, ctx->d_khat, nk * 6 * sizeof(float)));
+  long long ext = std::max<long long>({(long long)g.nx * g.ny * g.nz, (long long)g.kxn * g.ny * g.nz,
+                                       (long long)g.kxn * g.kyn * g.nz, (long long)nk});
+  double* b0 = nullptr;
+  double* b1 = nullptr;
+  double2* trig[3] = {nullptr, nullptr, nullptr};
+  int rc = MMP_OK;
+  rc = alloc_into(ctx, b0, (size_t)ext * 6 * sizeof(double));
+  if (rc == MMP_OK) rc = alloc_into(ctx, b1, (size_t)ext * 6 * sizeof(double));
+  const int P[3] = {g.Px, g.Py, g.Pz};
+  std::vector<double2> host[3];
+  for (int a = 0; a < 3 && rc == MMP_OK; ++a) {
+    host[a].resize(P[a]);
+    for (int t = 0; t < P[a]; ++t) {
+      double ang = 2.0 * 3.14159265358979323846 * (double)t / (double)P[a];
+      host[a][t] = make_double2(cos(ang), sin(ang));
+    }
+    rc = alloc_into(ctx, trig[a], P[a] * sizeof(double2));
+    if (rc == MMP_OK && cudaMemcpyAsync(trig[a], host[a].data(), P[a] * sizeof(double2),
+                                        cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+      rc = cuda_check(ctx, cudaGetLastError(), "upload trig");
+  }
+  if (rc == MMP_OK) {
+    KernelBuild kb;
+    kb.n[0] = g.nx; kb.n[1] = g.ny; kb.n[2] = g.nz;
+    kb.P[0] = g.Px; kb.P[1] = g.Py; kb.P[2] = g.Pz;
+    for (int a = 0; a < 3; ++a) { kb.cell[a] = ctx->cell[a]; kb.trig[a] = trig[a]; }
+    kb.rc = kRc;
+    kb.buf0 = b0;
+    kb.buf1 = b1;
+    kb.out = ctx->d_khat;
+    rc = cuda_check(ctx, build_kernel_spectrum(kb, ctx->stream), "demag kernel build");
+    if (rc == MMP_OK) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "demag kernel build (sync)");
+  }
+  dfree(ctx, b0);
+  dfree(ctx, b1);
+  for (int a = 0; a < 3; ++a) dfree(ctx, trig[a]);
+  if (rc == MMP_OK) ctx->khat_dirty = false;
+  return rc;
+}
+
+int validate_terms(mmp_ctx* ctx) {
+  if (ctx->nsub == 2 && has(ctx, MMP_T_DMI))
+    return fail(MMP_E_INVAL, "DMI with two sublattices is not supported (its boundary condition couples them)");
+  if (has(ctx, MMP_T_MEL) || has(ctx, MMP_T_ELASTIC)) {
+    // empty cells would need free elastic surfaces inside the grid
+    for (int s = 0; s < ctx->nsub; ++s)
+      for (int r = 0; r < MMP_MAX_REGIONS; ++r)
+        if (ctx->used[r] && ctx->scal[MMP_MS][s][r] == 0.0)
+          return fail(MMP_E_INVAL, "magnetoelastic/elastic terms need every cell magnetic (region %d has Ms = 0)", r);
+  }
+  if (has(ctx, MMP_T_DEMAG)) {
+    const Grid& g = ctx->g;
+    if (g.Px > 4096 || g.Py > 4096 || g.Pz > 32)
+      return fail(MMP_E_INVAL, "demag: padded lengths must be <= 4096 (x, y) and nz <= 16");
+  }
+  if (has(ctx, MMP_T_ELASTIC) && ctx->glob[MMP_RHO] <= 0.0)
+    return fail(MMP_E_INVAL, "elastic term needs a positive mass density");
+  if (has(ctx, MMP_T_AFM) && ctx->nsub != 2) return fail(MMP_E_INVAL, "AFM term needs two sublattices");
+  if (has(ctx, MMP_T_AFM) && ctx->glob[MMP_LATTICE_A] <= 0.0)
+    return fail(MMP_E_INVAL, "AFM term needs a positive lattice parameter");
+  return MMP_OK;
+}
+
+int prepare(mmp_ctx* ctx) {
+  TRY(validate_terms(ctx));
+  TRY(ensure_state(ctx));
+  TRY(upload_coefs(ctx));
+  if (has(ctx, MMP_T_DEMAG)) {
+    TRY(build_khat(ctx));
+    if (!ctx->d_T)
+      TRY(alloc_into(ctx, ctx->d_T, (size_t)ctx->g.kxn * 3 * ctx->g.nz * ctx->g.ny * sizeof(float2)));
+  }
+  if ((has(ctx, MMP_T_MEL) || has(ctx, MMP_T_ELASTIC)) && !ctx->d_eps) {
+    TRY(alloc_into(ctx, ctx->d_eps, (size_t)6 * ctx->g.n * sizeof(float)));
+    TRY(alloc_into(ctx, ctx->d_sig, (size_t)6 * ctx->g.n * sizeof(float)));
+  }
+  return MMP_OK;
+}
+
+DemagArgs demag_args(mmp_ctx* ctx) {
+  DemagArgs d;
+  d.T = ctx->d_T;
+  d.khat = ctx->d_khat;
+  d.tw_x = ctx->d_tw_x;
+  d.tw_y = ctx->d_tw_y;
+  d.tw_ly = ctx->d_tw_ly;
+  d.tw_z = ctx->d_tw_z;
+  d.plan_x = ctx->plan_x;
+  d.plan_ly = ctx->plan_ly;
+  d.R = ctx->R;
+  return d;
+}
+
+Coefs coefs(mmp_ctx* ctx) {
+  Coefs c;
+  c.reg = ctx->d_coef;
+  c.regions = ctx->d_regions;
+  c.hA = ctx->d_hA;
+  c.uniform = ctx->uniform ? 1 : 0;
+  return c;
+}
+
+// Bracket one launch with events when tracing is on.
+struct Traced {
+  mmp_ctx* ctx;
+  int k;
+  cudaEvent_t stop = nullptr;
+  Traced(mmp_ctx* c, int kernel) : ctx(c), k(kernel) {
+    if (!ctx->prof) return;
+    auto& v = ctx->prof_events[k];
+    if (ctx->prof_used[k] == v.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      v.push_back({a, b});
+    }
+    auto& pr = v[ctx->prof_used[k]++];
+    cudaEventRecord(pr.first, ctx->stream);
+    stop = pr.second;
+  }
+  ~Traced() {
+    if (stop) cudaEventRecord(stop, ctx->stream);
+  }
+};
+
+// One field evaluation.  With `sa.y` set the stage is assembled from it
+// into ctx->d_stage; otherwise `src` (the current state) is evaluated.
+int evaluate(mmp_ctx* ctx, StageArgs sa, const float* src, float* kout, float* Bout, unsigned* err,
+             const float* ecoef, const float* const* ek, int relax, unsigned* tmax) {
+  const Grid& g = ctx->g;
+  const bool demag = has(ctx, MMP_T_DEMAG);
+  const bool elastic = has(ctx, MMP_T_ELASTIC);
+  const bool strain = elastic || has(ctx, MMP_T_MEL);
+  DemagArgs d = demag_args(ctx);
+  Coefs co = coefs(ctx);
+  sa.stage = sa.y ? ctx->d_stage : const_cast<float*>(src);
+  sa.nparts = ctx->nparts;
+  sa.nsub = ctx->nsub;
+  const float* stage = sa.stage;
+  if (demag) {
+    { Traced t(ctx, MMP_K_PASS_A); CK(launch_passA(g, sa, d, co, ctx->thrA, ctx->stream), "pass A"); }
+    { Traced t(ctx, MMP_K_PASS_B); CK(launch_passB(g, d, ctx->thrB, ctx->stream), "pass B"); }
+  } else if (sa.y) {
+    Traced t(ctx, MMP_K_ASSEMBLE);
+    CK(launch_assemble(g, sa, ctx->stream), "assemble");
+  }
+  ElasticArgs ea;
+  ea.stage = stage;
+  ea.kout = kout;
+  ea.eps = ctx->d_eps;
+  ea.sig = ctx->d_sig;
+  ea.c11 = (float)ctx->glob[MMP_C11];
+  ea.c12 = (float)ctx->glob[MMP_C12];
+  ea.c44 = (float)ctx->glob[MMP_C44];
+  ea.eta = (float)ctx->glob[MMP_ETA];
+  ea.inv_rho = ctx->glob[MMP_RHO] > 0 ? (float)(1.0 / ctx->glob[MMP_RHO]) : 0.0f;
+  ea.terms = ctx->terms;
+  if (strain) { Traced t(ctx, MMP_K_STRAIN); CK(launch_strain(g, ea, ctx->nsub, ctx->stream), "strain"); }
+  FieldArgs f;
+  memset(&f, 0, sizeof f);
+  f.stage = stage;
+  f.kout = kout;
+  f.Bout = Bout;
+  f.eps = ctx->d_eps;
+  f.terms = ctx->terms;
+  f.err = err;
+  if (err) {
+    for (int j = 0; j < 7; ++j) f.ecoef[j] = ecoef[j];
+    for (int j = 0; j < 6; ++j) f.ek[j] = ek[j];
+  }
+  f.relax = relax;
+  f.torque_max = tmax;
+  { Traced t(ctx, MMP_K_FIELD); CK(launch_field(g, d, co, f, ctx->nsub, demag, ctx->thrC, ctx->stream), "field"); }
+  if (elastic) {
+    Traced t(ctx, MMP_K_ELASTIC);
+    CK(launch_elastic_rhs(g, ea, co, ctx->nsub, ctx->stream), "elastic");
+  }
+  ctx->evals++;
+  return MMP_OK;
+}
+
+int ensure_k1(mmp_ctx* ctx, int relax) {
+  if (ctx->k1_valid && ctx->k1_relax == relax) return MMP_OK;
+  StageArgs sa;
+  memset(&sa, 0, sizeof sa);
+  TRY(evaluate(ctx, sa, ctx->d_y, ctx->d_k[0], nullptr, nullptr, nullptr, nullptr, relax, nullptr));
+  ctx->k1_valid = true;
+  ctx->k1_relax = relax;
+  return MMP_OK;
+}
+
+// One DP45 attempt of size h.  With want_err the error estimate (and the
+// torque maximum at the new state) are read back (one synchronisation).
+int attempt(mmp_ctx* ctx, double h, bool want_err, int relax, double* err_out, double* tmax_out) {
+  TRY(ensure_k1(ctx, relax));
+  if (want_err) CK(cudaMemsetAsync(ctx->d_red, 0, 2 * sizeof(unsigned), ctx->stream), "reset error");
+  float ecoef[7];
+  for (int j = 0; j < 7; ++j) ecoef[j] = (float)(h * ((j < 6 ? kA[6][j] : 0.0) - kB4[j]));
+  const float* ek[6];
+  for (int j = 0; j < 6; ++j) ek[j] = ctx->d_k[j];
+  for (int i = 1; i <= 6; ++i) {
+    StageArgs sa;
+    memset(&sa, 0, sizeof sa);
+    sa.y = ctx->d_y;
+    sa.nk = i;
+    for (int j = 0; j < i; ++j) {
+      sa.k[j] = ctx->d_k[j];
+      sa.coef[j] = (float)(h * kA[i][j]);
+    }
+    sa.normalize = (i == 6);
+    bool last = (i == 6);
+    TRY(evaluate(ctx, sa, nullptr, ctx->d_k[i], nullptr, last && want_err ? ctx->d_red : nullptr, ecoef, ek,
+                 relax, last && want_err ? ctx->d_red + 1 : nullptr));
+  }
+  if (want_err) {
+    CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream),
+       "read error");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    float e, tm;
+    memcpy(&e, &ctx->h_red[0], 4);
+    memcpy(&tm, &ctx->h_red[1], 4);
+    *err_out = e;
+    if (tmax_out) *tmax_out = tm;
+  }
+  return MMP_OK;
+}
+
+void accept(mmp_ctx* ctx, double h) {
+  std::swap(ctx->d_y, ctx->d_stage);
+  std::swap(ctx->d_k[0], ctx->d_k[6]);
+  ctx->k1_valid = true;
+  ctx->t += h;
+  ctx->steps++;
+}
+
+double grow(double err, double tol) {
+  double fac = err == 0.0 ? kGrowMax : kSafety * pow(tol / err, kExponent);
+  return std::min(std::max(fac, kGrowMin), kGrowMax);
+}
+
+// Advance: nsteps attempts-limited loop.  `until` < 0: count accepted steps.
+int advance(mmp_ctx* ctx, long long nsteps, double until, int relax, double torque_tol, double timeout_s,
+            bool* converged) {
+  TRY(prepare(ctx));
+  auto t0 = std::chrono::steady_clock::now();
+  long long done = 0;
+  const bool adaptive = ctx->adaptive || relax;
+  while (true) {
+    if (until >= 0.0) {
+      if (ctx->t >= until * (1.0 - 1e-15)) break;
+    } else if (done >= nsteps) {
+      break;
+    }
+    double h = ctx->dt;
+    if (until >= 0.0 && ctx->t + h > until) h = until - ctx->t;
+    if (!adaptive) {
+      double err = 0.0;
+      TRY(attempt(ctx, h, false, relax, &err, nullptr));
+      accept(ctx, h);
+      ++done;
+      continue;
+    }
+    double err = 0.0, tm = 0.0;
+    TRY(attempt(ctx, h, true, relax, &err, &tm));
+    if (!std::isfinite(err)) {
+      ctx->k1_valid = true;   // state and k1 untouched
+      return fail(MMP_E_NONFINITE, "non-finite error estimate at t = %g s (dt = %g s)", ctx->t, h);
+    }
+    bool ok = err <= ctx->tol || h <= ctx->dt_min;
+    double fac = grow(err, ctx->tol);
+    if (ok) {
+      accept(ctx, h);
+      ++done;
+    } else {
+      ctx->rejected++;
+    }
+    ctx->dt = std::min(std::max(h * fac, ctx->dt_min), ctx->dt_max);
+    if (relax && ok && tm <= torque_tol) {
+      if (converged) *converged = true;
+      break;
+    }
+    if (timeout_s > 0) {
+      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > timeout_s) return fail(MMP_E_TIMEOUT, "relax did not converge within %g s", timeout_s);
+    }
+  }
+  if (!adaptive) CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return MMP_OK;
+}
+
+}  // namespace
+
+// ============================================================== C-ABI =====
+extern "C" {
+
+int mmp_version(void) { return MMP_VERSION; }
+
+const char* mmp_last_error(void) { return g_err.c_str(); }
+
+int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, double cz, int nsub,
+               void* stream, mmp_alloc_fn alloc, mmp_free_fn dealloc, void* user) {
+  g_err.clear();
+  if (!out) return fail(MMP_E_INVAL, "out is null");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(MMP_E_INVAL, "grid extents must be >= 1");
+  if (!(cx > 0) || !(cy > 0) || !(cz > 0)) return fail(MMP_E_INVAL, "cell sizes must be > 0");
+  if (nsub != 1 && nsub != 2) return fail(MMP_E_INVAL, "n_sublattices must be 1 or 2");
+  if ((alloc == nullptr) != (dealloc == nullptr)) return fail(MMP_E_INVAL, "give both allocator functions or none");
+  long long n = (long long)nx * ny * nz;
+  if (n > (1LL << 31)) return fail(MMP_E_INVAL, "grid too large");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MMP_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+  mmp_ctx* ctx = new mmp_ctx();
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->ualloc = alloc;
+  ctx->ufree = dealloc;
+  ctx->uuser = user;
+  ctx->nsub = nsub;
+  ctx->cell[0] = cx; ctx->cell[1] = cy; ctx->cell[2] = cz;
+  memset(ctx->scal, 0, sizeof ctx->scal);
+  memset(ctx->vec, 0, sizeof ctx->vec);
+  memset(ctx->glob, 0, sizeof ctx->glob);
+  for (int s = 0; s < 2; ++s)
+    for (int r = 0; r < MMP_MAX_REGIONS; ++r) {
+      ctx->vec[MMP_ANIS_U][s][r][2] = 1.0;
+      ctx->vec[MMP_ANIS_UB][s][r][0] = 1.0;
+    }
+  Grid& g = ctx->g;
+  g.nx = nx; g.ny = ny; g.nz = nz; g.n = n;
+  g.Px = nice_length(nx); g.Py = nice_length(ny); g.Pz = nice_length(nz);
+  g.kxn = g.Px / 2 + 1; g.kyn = g.Py / 2 + 1; g.kzn = g.Pz / 2 + 1;
+  for (int a = 0; a < 3; ++a) {
+    g.h[a] = (float)ctx->cell[a];
+    g.ih[a] = (float)(1.0 / ctx->cell[a]);
+  }
+  // pass B: split ky into R residue classes so that a plane stays <= ~100 KB
+  ctx->R = 1;
+  while (ctx->R < 8 && (size_t)3 * nz * (g.Py / ctx->R) * sizeof(float2) > 100 * 1024 && g.Py % (2 * ctx->R) == 0 &&
+         g.Py / (2 * ctx->R) >= 2)
+    ctx->R *= 2;
+  bool ok = make_plan(g.Px, ctx->plan_x) && make_plan(g.Py / ctx->R, ctx->plan_ly);
+  if (!ok) { delete ctx; return fail(MMP_E_INVAL, "unsupported FFT length"); }
+  auto r32 = [](long long v) { return (int)((v + 31) / 32 * 32); };
+  ctx->thrA = std::min(512, std::max(128, r32((long long)MMP_NP * g.Px / 32)));
+  long long elB = (long long)3 * nz * (g.Py / ctx->R);
+  ctx->thrB = std::min(512, std::max(64, r32(std::max(elB / 32, (long long)(g.Py / ctx->R)))));
+  ctx->thrC = std::min(512, std::max(std::max(128, r32((long long)MMP_NP * g.Px / 32)),
+                                     r32((long long)MMP_TY * nx / 8)));
+  int rc = MMP_OK;
+#define CR(x) do { if (rc == MMP_OK) rc = (x); } while (0)
+  CR(alloc_into(ctx, ctx->d_coef, 2 * MMP_MAX_REGIONS * sizeof(RegionCoef)));
+  CR(alloc_into(ctx, ctx->d_red, 2 * sizeof(unsigned)));
+  if (rc == MMP_OK && cudaMallocHost(&ctx->h_red, 2 * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    rc = fail(MMP_E_OOM, "pinned allocation failed");
+  }
+  auto up = [&](float2*& dst, int P) {
+    if (rc != MMP_OK) return;
+    std::vector<float2> w = roots(P);
+    rc = alloc_into(ctx, dst, P * sizeof(float2));
+    if (rc == MMP_OK)
+      rc = cuda_check(ctx, cudaMemcpy(dst, w.data(), P * sizeof(float2), cudaMemcpyHostToDevice), "twiddles");
+  };
+  up(ctx->d_tw_x, g.Px);
+  up(ctx->d_tw_y, g.Py);
+  up(ctx->d_tw_ly, g.Py / ctx->R);
+  up(ctx->d_tw_z, g.Pz);
+#undef CR
+  if (rc == MMP_OK) rc = ensure_state(ctx);
+  if (rc != MMP_OK) {
+    std::string msg = g_err;
+    mmp_destroy(ctx);
+    g_err = msg;
+    return rc;
+  }
+  *out = ctx;
+  return MMP_OK;
+}
+
+int mmp_destroy(mmp_ctx* ctx) {
+  if (!ctx) return MMP_OK;
+  cudaStreamSynchronize(ctx->stream);
+  void* bufs[] = {ctx->d_regions, ctx->d_coef, ctx->d_hA, ctx->d_y, ctx->d_stage, ctx->d_B, ctx->d_eps,
+                  ctx->d_sig, ctx->d_T, ctx->d_khat, ctx->d_tw_x, ctx->d_tw_y, ctx->d_tw_ly, ctx->d_tw_z,
+                  ctx->d_red};
+  for (void* p : bufs) dfree(ctx, p);
+  for (int i = 0; i < 7; ++i) dfree(ctx, ctx->d_k[i]);
+  if (ctx->h_red) cudaFreeHost(ctx->h_red);
+  for (int k = 0; k < MMP_NKERNEL; ++k)
+    for (auto& pr : ctx->prof_events[k]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  delete ctx;
+  return MMP_OK;
+}
+
+int mmp_set_region_map(mmp_ctx* ctx, const uint8_t* regions) {
+  TRY(check_ctx(ctx));
+  if (!regions) return fail(MMP_E_INVAL, "regions is null");
+  const long long n = ctx->g.n;
+  std::vector<uint8_t> host(n);
+  CK(cudaMemcpyAsync(host.data(), regions, n, cudaMemcpyDefault, ctx->stream), "copy regions");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  bool uni = std::all_of(host.begin(), host.end(), [](uint8_t r) { return r == 0; });
+  for (int r = 0; r < MMP_MAX_REGIONS; ++r) ctx->used[r] = false;
+  for (uint8_t r : host) ctx->used[r] = true;
+  if (!ctx->d_regions) TRY(alloc_into(ctx, ctx->d_regions, n));
+  CK(cudaMemcpyAsync(ctx->d_regions, host.data(), n, cudaMemcpyHostToDevice, ctx->stream), "upload regions");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->uniform = uni;
+  ctx->coef_dirty = true;
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+int mmp_set_param(mmp_ctx* ctx, int sub, int param, int region, double value) {
+  TRY(check_ctx(ctx));
+  if (param < 0 || param >= MMP_NPARAM) return fail(MMP_E_INVAL, "unknown parameter %d", param);
+  if (sub < -1 || sub >= ctx->nsub) return fail(MMP_E_INVAL, "bad sublattice %d", sub);
+  if (region < -1 || region >= MMP_MAX_REGIONS) return fail(MMP_E_INVAL, "bad region %d", region);
+  if (!std::isfinite(value)) return fail(MMP_E_INVAL, "non-finite value");
+  if (param == MMP_MS && value < 0) return fail(MMP_E_INVAL, "Ms must be >= 0");
+  for (int s = 0; s < ctx->nsub; ++s) {
+    if (sub >= 0 && s != sub) continue;
+    for (int r = 0; r < MMP_MAX_REGIONS; ++r)
+      if (region < 0 || r == region) ctx->scal[param][s][r] = value;
+  }
+  ctx->coef_dirty = true;
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+int mmp_set_param3(mmp_ctx* ctx, int sub, int param, int region, double x, double y, double z) {
+  TRY(check_ctx(ctx));
+  if (param < 0 || param >= MMP_NPARAM3) return fail(MMP_E_INVAL, "unknown vector parameter %d", param);
+  if (sub < -1 || sub >= ctx->nsub) return fail(MMP_E_INVAL, "bad sublattice %d", sub);
+  if (region < -1 || region >= MMP_MAX_REGIONS) return fail(MMP_E_INVAL, "bad region %d", region);
+  if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z)) return fail(MMP_E_INVAL, "non-finite value");
+  for (int s = 0; s < ctx->nsub; ++s) {
+    if (sub >= 0 && s != sub) continue;
+    for (int r = 0; r < MMP_MAX_REGIONS; ++r)
+      if (region < 0 || r == region) {
+        ctx->vec[param][s][r][0] = x;
+        ctx->vec[param][s][r][1] = y;
+        ctx->vec[param][s][r][2] = z;
+      }
+  }
+  ctx->coef_dirty = true;
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+int mmp_set_global(mmp_ctx* ctx, int param, double value) {
+  TRY(check_ctx(ctx));
+  if (param < 0 || param >= MMP_NGLOBAL) return fail(MMP_E_INVAL, "unknown global %d", param);
+  if (!std::isfinite(value)) return fail(MMP_E_INVAL, "non-finite value");
+  ctx->glob[param] = value;
+  ctx->coef_dirty = true;
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+int mmp_enable_terms(mmp_ctx* ctx, unsigned terms) {
+  TRY(check_ctx(ctx));
+  if (terms & ~255u) return fail(MMP_E_INVAL, "unknown term bits 0x%x", terms);
+  ctx->terms = terms;
+  ctx->k1_valid = false;
+  return ensure_state(ctx);
+}
+
+int mmp_set_m(mmp_ctx* ctx, int sub, const float* m, int normalize) {
+  TRY(check_ctx(ctx));
+  if (sub < 0 || sub >= ctx->nsub) return fail(MMP_E_INVAL, "bad sublattice %d", sub);
+  if (!m) return fail(MMP_E_INVAL, "m is null");
+  TRY(ensure_state(ctx));
+  float* dst = ctx->d_y + 3LL * sub * ctx->g.n;
+  CK(cudaMemcpyAsync(dst, m, 3LL * ctx->g.n * sizeof(float), cudaMemcpyDefault, ctx->stream), "copy m");
+  if (normalize) CK(launch_normalize(dst, ctx->g.n, ctx->stream), "normalize");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+int mmp_get_m(mmp_ctx* ctx, int sub, float* m) {
+  TRY(check_ctx(ctx));
+  if (sub < 0 || sub >= ctx->nsub) return fail(MMP_E_INVAL, "bad sublattice %d", sub);
+  if (!m) return fail(MMP_E_INVAL, "m is null");
+  CK(cudaMemcpyAsync(m, ctx->d_y + 3LL * sub * ctx->g.n, 3LL * ctx->g.n * sizeof(float), cudaMemcpyDefault,
+                     ctx->stream),
+     "copy m");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return MMP_OK;
+}
+
+int mmp_set_elastic(mmp_ctx* ctx, const float* u, const float* v) {
+  TRY(check_ctx(ctx));
+  if (!has(ctx, MMP_T_ELASTIC)) return fail(MMP_E_STATE, "enable MMP_T_ELASTIC first");
+  TRY(ensure_state(ctx));
+  const long long n3 = 3LL * ctx->g.n;
+  float* base = ctx->d_y + 3LL * ctx->nsub * ctx->g.n;
+  if (u) CK(cudaMemcpyAsync(base, u, n3 * sizeof(float), cudaMemcpyDefault, ctx->stream), "copy u");
+  if (v) CK(cudaMemcpyAsync(base + n3, v, n3 * sizeof(float), cudaMemcpyDefault, ctx->stream), "copy v");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+int mmp_get_elastic(mmp_ctx* ctx, float* u, float* v) {
+  TRY(check_ctx(ctx));
+  if (!has(ctx, MMP_T_ELASTIC)) return fail(MMP_E_STATE, "elastic term is off");
+  const long long n3 = 3LL * ctx->g.n;
+  const float* base = ctx->d_y + 3LL * ctx->nsub * ctx->g.n;
+  if (u) CK(cudaMemcpyAsync(u, base, n3 * sizeof(float), cudaMemcpyDefault, ctx->stream), "copy u");
+  if (v) CK(cudaMemcpyAsync(v, base + n3, n3 * sizeof(float), cudaMemcpyDefault, ctx->stream), "copy v");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return MMP_OK;
+}
+
+int mmp_set_solver(mmp_ctx* ctx, int method, int adaptive, double dt, double tol, double dt_min, double dt_max) {
+  TRY(check_ctx(ctx));
+  if (method != MMP_DP45) return fail(MMP_E_INVAL, "unknown method %d", method);
+  if (!(dt > 0) || !(dt_min > 0) || !(dt_max >= dt_min) || (adaptive && !(tol > 0)))
+    return fail(MMP_E_INVAL, "bad solver settings");
+  ctx->adaptive = adaptive ? 1 : 0;
+  ctx->dt = dt;
+  ctx->tol = tol;
+  ctx->dt_min = dt_min;
+  ctx->dt_max = dt_max;
+  return MMP_OK;
+}
+
+int mmp_eval_field(mmp_ctx* ctx, int sub, float* B, float* tau) {
+  TRY(check_ctx(ctx));
+  if (sub < 0 || sub >= ctx->nsub) return fail(MMP_E_INVAL, "bad sublattice %d", sub);
+  TRY(prepare(ctx));
+  if (B && !ctx->d_B) TRY(alloc_into(ctx, ctx->d_B, 3LL * ctx->nsub * ctx->g.n * sizeof(float)));
+  StageArgs sa;
+  memset(&sa, 0, sizeof sa);
+  TRY(evaluate(ctx, sa, ctx->d_y, ctx->d_k[0], B ? ctx->d_B : nullptr, nullptr, nullptr, nullptr, 0, nullptr));
+  ctx->k1_valid = true;
+  ctx->k1_relax = 0;
+  const long long n3 = 3LL * ctx->g.n;
+  if (B) CK(cudaMemcpyAsync(B, ctx->d_B + sub * n3, n3 * sizeof(float), cudaMemcpyDefault, ctx->stream), "copy B");
+  if (tau)
+    CK(cudaMemcpyAsync(tau, ctx->d_k[0] + sub * n3, n3 * sizeof(float), cudaMemcpyDefault, ctx->stream),
+       "copy tau");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return MMP_OK;
+}
+
+int mmp_step(mmp_ctx* ctx, int nsteps) {
+  TRY(check_ctx(ctx));
+  if (nsteps < 0) return fail(MMP_E_INVAL, "nsteps < 0");
+  return advance(ctx, nsteps, -1.0, 0, 0.0, 0.0, nullptr);
+}
+
+int mmp_run(mmp_ctx* ctx, double duration) {
+  TRY(check_ctx(ctx));
+  if (!(duration >= 0)) return fail(MMP_E_INVAL, "duration must be >= 0");
+  return advance(ctx, 0, ctx->t + duration, 0, 0.0, 0.0, nullptr);
+}
+
+int mmp_relax(mmp_ctx* ctx, double torque_tol, double max_time, double timeout_s) {
+  TRY(check_ctx(ctx));
+  if (!(torque_tol > 0) || !(max_time > 0)) return fail(MMP_E_INVAL, "bad relax settings");
+  bool conv = false;
+  int rc = advance(ctx, 0, ctx->t + max_time, 1, torque_tol, timeout_s, &conv);
+  ctx->k1_valid = false;   // k1 holds the damping-only torque
+  return rc;
+}
+
+int mmp_get_time(mmp_ctx* ctx, double* t, double* dt, long long* steps, long long* rejected, long long* evals) {
+  TRY(check_ctx(ctx));
+  if (t) *t = ctx->t;
+  if (dt) *dt = ctx->dt;
+  if (steps) *steps = ctx->steps;
+  if (rejected) *rejected = ctx->rejected;
+  if (evals) *evals = ctx->evals;
+  return MMP_OK;
+}
+
+namespace {
+struct BlobHeader {
+  char magic[8];
+  int version, nsub, nparts, pad;
+  long long n, steps, rejected, evals;
+  double t, dt;
+};
+}  // namespace
+
+int mmp_get_state(mmp_ctx* ctx, void* blob, size_t* size) {
+  TRY(check_ctx(ctx));
+  if (!size) return fail(MMP_E_INVAL, "size is null");
+  TRY(ensure_state(ctx));
+  size_t need = sizeof(BlobHeader) + ctx->nstate * sizeof(float);
+  if (!blob) { *size = need; return MMP_OK; }
+  if (*size < need) return fail(MMP_E_INVAL, "blob too small (%zu < %zu)", *size, need);
+  BlobHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, "MMPSTATE", 8);
+  h.version = MMP_VERSION;
+  h.nsub = ctx->nsub;
+  h.nparts = ctx->nparts;
+  h.n = ctx->g.n;
+  h.steps = ctx->steps;
+  h.rejected = ctx->rejected;
+  h.evals = ctx->evals;
+  h.t = ctx->t;
+  h.dt = ctx->dt;
+  memcpy(blob, &h, sizeof h);
+  CK(cudaMemcpyAsync(static_cast<char*>(blob) + sizeof h, ctx->d_y, ctx->nstate * sizeof(float),
+                     cudaMemcpyDeviceToHost, ctx->stream),
+     "copy state");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  *size = need;
+  return MMP_OK;
+}
+
+int mmp_set_state(mmp_ctx* ctx, const void* blob, size_t size) {
+  TRY(check_ctx(ctx));
+  if (!blob || size < sizeof(BlobHeader)) return fail(MMP_E_INVAL, "blob too small");
+  BlobHeader h;
+  memcpy(&h, blob, sizeof h);
+  if (memcmp(h.magic, "MMPSTATE", 8) != 0 || h.version != MMP_VERSION) return fail(MMP_E_INVAL, "not a state blob");
+  TRY(ensure_state(ctx));
+  if (h.nsub != ctx->nsub || h.nparts != ctx->nparts || h.n != ctx->g.n)
+    return fail(MMP_E_INVAL, "state blob does not match the context");
+  if (size < sizeof h + ctx->nstate * sizeof(float)) return fail(MMP_E_INVAL, "blob truncated");
+  CK(cudaMemcpyAsync(ctx->d_y, static_cast<const char*>(blob) + sizeof h, ctx->nstate * sizeof(float),
+                     cudaMemcpyHostToDevice, ctx->stream),
+     "copy state");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->t = h.t;
+  ctx->dt = h.dt;
+  ctx->steps = h.steps;
+  ctx->rejected = h.rejected;
+  ctx->evals = h.evals;
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+int mmp_profile(mmp_ctx* ctx, int enable) {
+  TRY(check_ctx(ctx));
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  for (int k = 0; k < MMP_NKERNEL; ++k) ctx->prof_used[k] = 0;
+  ctx->prof = enable != 0;
+  return MMP_OK;
+}
+
+int mmp_profile_read(mmp_ctx* ctx, int kernel, long long* launches, double* total_ms) {
+  TRY(check_ctx(ctx));
+  if (kernel < 0 || kernel >= MMP_NKERNEL) return fail(MMP_E_INVAL, "unknown kernel %d", kernel);
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  double tot = 0.0;
+  for (size_t i = 0; i < ctx->prof_used[kernel]; ++i) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, ctx->prof_events[kernel][i].first, ctx->prof_events[kernel][i].second),
+       "event time");
+    tot += ms;
+  }
+  if (launches) *launches = (long long)ctx->prof_used[kernel];
+  if (total_ms) *total_ms = tot;
+  return MMP_OK;
+}
+
+int mmp_sync(mmp_ctx* ctx) {
+  TRY(check_ctx(ctx));
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return MMP_OK;
+}
+
+}  // extern "C"

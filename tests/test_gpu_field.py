@@ -1,0 +1,85 @@
+"""Parity of one field + torque evaluation of the CUDA path (through the
+C-ABI) with the FP64 oracle, element by element, on seeded inputs.
+
+Sizes span several x/y tiles with ragged tails, padded lengths 2^k and
+3*2^k, the pass-B cluster split of large ky planes (R = 2, 4), the fixed and
+generic z transforms (nz = 1, 2, 4, 8 and 3), axes of one cell, several
+regions with empty cells, and the two-sublattice magnetoelastic path."""
+import numpy as np
+import pytest
+
+from inputs import config_small
+from gpu_util import field_tolerance, torque_tolerance, make_magnet, gpu_eval, oracle_eval
+
+pytestmark = pytest.mark.gpu
+
+FM = ("DEMAG", "EXCH", "ANIS", "DMI", "ZEEMAN")
+
+CASES = [
+    # shape, cell, seed, terms, regions, empty fraction
+    ((5, 4, 3), (2e-9, 3e-9, 1.5e-9), 1, FM, 1, 0.0),
+    ((17, 9, 1), (2e-9, 2e-9, 2e-9), 2, FM, 1, 0.0),
+    ((24, 20, 2), (3e-9, 2e-9, 1e-9), 3, FM, 3, 0.1),
+    ((64, 64, 1), (4e-9, 4e-9, 4e-9), 4, ("DEMAG", "EXCH", "ZEEMAN"), 1, 0.0),
+    ((33, 19, 8), (2e-9, 2e-9, 1e-9), 5, FM, 1, 0.0),
+    ((16, 300, 8), (2e-9, 2e-9, 1e-9), 6, FM, 1, 0.0),      # ky split R = 2
+    ((8, 600, 4), (2e-9, 2e-9, 1e-9), 7, FM, 2, 0.0),       # R = 2, Py = 1536
+    ((4, 1100, 4), (2e-9, 2e-9, 2e-9), 8, FM, 1, 0.0),      # R = 4, Py = 3072
+    ((10, 6, 3), (2e-9, 2e-9, 1e-9), 9, FM, 1, 0.0),        # generic nz
+    ((1, 1, 1), (3e-9, 3e-9, 3e-9), 10, FM, 1, 0.0),
+    ((1, 7, 1), (2e-9, 2e-9, 2e-9), 11, FM, 1, 0.0),
+    ((9, 1, 2), (2e-9, 2e-9, 2e-9), 12, FM, 1, 0.0),
+    ((40, 12, 1), (2e-9, 2e-9, 2e-9), 13, ("EXCH", "DMI", "ANIS"), 4, 0.15),   # no demag
+]
+
+
+@pytest.mark.parametrize("shape,cell,seed,terms,nreg,empty", CASES,
+                         ids=["x".join(map(str, c[0])) + "-%d" % c[2] for c in CASES])
+def test_field_and_torque_parity(shape, cell, seed, terms, nreg, empty):
+    w = config_small(shape, cell, seed, terms=terms, n_regions=nreg, empty_fraction=empty)
+    p = w.problem
+    mag = make_magnet(p, w.m0)
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0)
+    tolB = field_tolerance(p, Bo[0])
+    assert np.all(np.abs(Bg[0] - Bo[0]) <= tolB), np.abs(Bg[0] - Bo[0]).max()
+    tolT = torque_tolerance(p, Bo[0], tolB)
+    assert np.all(np.abs(Tg[0] - To[0]) <= tolT), np.abs(Tg[0] - To[0]).max()
+    mag.close()
+
+
+def test_two_sublattice_magnetoelastic_parity():
+    w = config_small((23, 18, 1), (2e-9, 2e-9, 2e-9), 31, n_sub=2,
+                     terms=("DEMAG", "EXCH", "ANIS", "AFM", "MEL", "ELASTIC", "ZEEMAN"))
+    p = w.problem
+    p.set("DIND", 0.0)
+    rng = np.random.default_rng(5)
+    u = (rng.normal(size=(3, 1, 18, 23)) * 2e-12).astype(np.float32)
+    v = np.zeros_like(u)
+    mag = make_magnet(p, w.m0, u, v)
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0, u)
+    for s in range(2):
+        tolB = field_tolerance(p, Bo[s])
+        assert np.all(np.abs(Bg[s] - Bo[s]) <= tolB), (s, np.abs(Bg[s] - Bo[s]).max())
+        tolT = torque_tolerance(p, Bo[s], tolB)
+        assert np.all(np.abs(Tg[s] - To[s]) <= tolT), (s, np.abs(Tg[s] - To[s]).max())
+    mag.close()
+
+
+def test_large_random_exchange_field_within_bar():
+    """Random m on 2x2x1 nm cells with A = 1.6e-11 gives |B_exch| up to
+    ~1.7e2 T; the double-float exchange sum keeps the error under the
+    1e-5 mu0 Ms bar (which is below one FP32 ulp of such fields)."""
+    w = config_small((40, 36, 8), (2e-9, 2e-9, 1e-9), 41, terms=("EXCH", "DMI", "ANIS", "DEMAG"))
+    p = w.problem
+    p.set("MS", 1.1e6).set("AEX", 1.6e-11).set("DIND", 3e-3).set("KU1", 8e5).set("KU2", 0.0)
+    p.set("KB1", 0.0).set("ANIS_U", (0.0, 0.0, 1.0))
+    mag = make_magnet(p, w.m0)
+    Bg, _ = gpu_eval(mag, p)
+    Bo, _ = oracle_eval(p, w.m0)
+    from inputs import MU0
+    bar = 1e-5 * MU0 * 1.1e6
+    assert np.abs(Bo[0]).max() > 100.0
+    assert np.abs(Bg[0] - Bo[0]).max() <= bar
+    mag.close()
