@@ -329,6 +329,23 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_evals(args):
+    """Set-up plus N field evaluations and N DP45 attempts of the same
+    workload, without timing (a short command for ncu captures)."""
+    import torch
+    import paper_2411_18194_gb300 as pkg
+    from inputs import config_c2
+    w = config_c2()
+    mag = pkg.Magnet.from_problem(w.problem)
+    mag.set_m(0, torch.from_numpy(w.m0[0]).cuda())
+    mag.set_solver(adaptive=True, dt=w.dt, tol=w.tol)
+    for _ in range(args.profile_evals):
+        mag.eval_field(0)
+        mag.step(1)
+    mag.sync()
+    mag.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,9 +353,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-evals", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
+    if args.profile_evals:
+        run_profile_evals(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -20,6 +20,13 @@ struct FftPlan {
   int n16, n8, n4, n2, n3;
 };
 
+// Shared-memory layout of a batch of transforms: element i of transform t
+// sits at t * fft_pitch(L) + i + i/32.  One padding slot per 32 elements
+// turns the stride-R stores of the early Stockham passes into distinct
+// banks; the odd pitch staggers the starts of successive transforms.
+__host__ __device__ __forceinline__ int fft_pitch(int L) { return L + (L >> 5) + 1; }
+__device__ __forceinline__ int fidx(int t, int i, int pitch) { return t * pitch + i + (i >> 5); }
+
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -134,7 +141,9 @@ template <int R, int CAP>
 struct PassCap { static constexpr int B = (R == 3) ? CAP / 3 : CAP / R; };
 
 // One in-place Stockham pass of radix R over `nbatch` transforms of length L
-// stored contiguously in shared memory (transform t at data + t*L).
+// held in shared memory with the padded layout above.  Ns (the product of
+// the radices already applied) is a power of two for every pass of the
+// plans used here (the one radix-3 pass comes last on lengths 3*2^a).
 // Requires L*nbatch <= (CAP/R)*R*blockDim.x (checked by the host).
 template <int R, bool INV, int CAP>
 __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, int Ns,
@@ -143,15 +152,19 @@ __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, i
   const int nbf = L / R;
   const int total = nbf * nbatch;
   const int tstride = L / (Ns * R);
+  const int pitch = fft_pitch(L);
+  // t = b / nbf without an integer division: (b + 1/2) / nbf is at least
+  // 1/(2 nbf) away from an integer and b, nbf < 2^15, so the FP32 quotient
+  // truncates exactly.
+  const float rnbf = 1.0f / (float)nbf;
   float2 v[MAXB][R];
 #pragma unroll
   for (int i = 0; i < MAXB; ++i) {
     int b = threadIdx.x + i * blockDim.x;
     if (b < total) {
-      int t = b / nbf, j = b - t * nbf;
-      const float2* src = data + t * L + j;
+      int t = (int)(((float)b + 0.5f) * rnbf), j = b - t * nbf;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = src[r * nbf];
+      for (int r = 0; r < R; ++r) v[i][r] = data[fidx(t, j + r * nbf, pitch)];
     }
   }
   __syncthreads();
@@ -159,8 +172,8 @@ __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, i
   for (int i = 0; i < MAXB; ++i) {
     int b = threadIdx.x + i * blockDim.x;
     if (b < total) {
-      int t = b / nbf, j = b - t * nbf;
-      int k = j % Ns;
+      int t = (int)(((float)b + 0.5f) * rnbf), j = b - t * nbf;
+      int k = j & (Ns - 1);
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -170,9 +183,9 @@ __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, i
         }
       }
       dft<R, INV>(v[i]);
-      float2* dst = data + t * L + (j / Ns) * Ns * R + k;
+      const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[r * Ns] = v[i][r];
+      for (int r = 0; r < R; ++r) data[fidx(t, o + r * Ns, pitch)] = v[i][r];
     }
   }
   __syncthreads();

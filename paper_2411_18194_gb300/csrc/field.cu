@@ -180,6 +180,7 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
 __device__ __forceinline__ void inverse_x_component(int c, float2* fbuf, float* bd, const Grid& g,
                                                     const DemagArgs& d, int z, int y0) {
   const int nx = g.nx, ny = g.ny, Px = g.Px;
+  const int pitch = fft_pitch(Px);
   for (int e = threadIdx.x; e < MMP_NP * Px; e += blockDim.x) {
     int k = e / MMP_NP, p = e - k * MMP_NP;
     int kk = k <= Px / 2 ? k : Px - k;
@@ -188,13 +189,13 @@ __device__ __forceinline__ void inverse_x_component(int c, float2* fbuf, float* 
     float2 xa = ya < ny ? Tc[ya] : make_float2(0.0f, 0.0f);
     float2 xb = yb < ny ? Tc[yb] : make_float2(0.0f, 0.0f);
     if (k > Px / 2) { xa.y = -xa.y; xb.y = -xb.y; }
-    fbuf[p * Px + k] = make_float2(xa.x - xb.y, xa.y + xb.x);
+    fbuf[fidx(p, k, pitch)] = make_float2(xa.x - xb.y, xa.y + xb.x);
   }
   __syncthreads();
   block_fft<true>(fbuf, d.plan_x, MMP_NP, d.tw_x);
   for (int e = threadIdx.x; e < MMP_TY * nx; e += blockDim.x) {
     int row = e / nx, x = e - row * nx;
-    float2 v = fbuf[(row >> 1) * Px + x];
+    float2 v = fbuf[fidx(row >> 1, x, pitch)];
     bd[(c * MMP_TY + row) * nx + x] = (row & 1) ? v.y : v.x;
   }
   __syncthreads();
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(512) k_field(Grid g, DemagArgs d, Coefs co, Fi
 
 size_t smem_field(const Grid& g, bool demag) {
   if (!demag) return 0;
-  return (size_t)((3 * MMP_TY * g.nx + 3) & ~3) * sizeof(float) + (size_t)MMP_NP * g.Px * sizeof(float2);
+  return (size_t)((3 * MMP_TY * g.nx + 3) & ~3) * sizeof(float) + (size_t)MMP_NP * fft_pitch(g.Px) * sizeof(float2);
 }
 
 cudaError_t launch_field(const Grid& g, const DemagArgs& d, const Coefs& c, const FieldArgs& f, int nsub,

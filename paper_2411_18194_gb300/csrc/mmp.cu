@@ -14,6 +14,7 @@
 
 #include "kernels.h"
 #include "mmp.h"
+#include "plan.h"
 
 using namespace mmp;
 
@@ -45,40 +46,6 @@ const double kB4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 
 // step-size controller (a reading of what the paper leaves open)
 const double kSafety = 0.9, kGrowMin = 0.2, kGrowMax = 5.0, kExponent = 0.2;
 const double kRc = 10.0;   // Newell below 10 max(cell), asymptotic above
-
-int nice_length(int n) {
-  // smallest even 2^a or 3*2^a >= 2n - 1 (1 when n == 1)
-  if (n == 1) return 1;
-  int best = 1 << 30;
-  for (int p = 2; p < (1 << 30); p *= 2)
-    if (p >= 2 * n - 1) { best = std::min(best, p); break; }
-  for (int p = 6; p < (1 << 30); p *= 2)
-    if (p >= 2 * n - 1) { best = std::min(best, p); break; }
-  return best;
-}
-
-bool make_plan(int L, FftPlan& p) {
-  p.L = L;
-  p.n16 = p.n8 = p.n4 = p.n2 = p.n3 = 0;
-  int r = L, a = 0;
-  while (r % 3 == 0) { r /= 3; p.n3++; }
-  while (r % 2 == 0) { r /= 2; a++; }
-  if (r != 1) return false;
-  p.n16 = a / 4;
-  p.n8 = (a % 4) == 3;
-  p.n4 = (a % 4) == 2;
-  p.n2 = (a % 4) == 1;
-  return true;
-}
-
-std::vector<float2> roots(int P) {
-  std::vector<float2> w(P);
-  for (int t = 0; t < P; ++t) {
-    double a = 2.0 * 3.14159265358979323846 * (double)t / (double)P;
-    w[t] = make_float2((float)cos(a), (float)(-sin(a)));
-  }
-  return w;
-}
 
 float2 split(double v) {
   float hi = (float)v;
@@ -630,19 +597,10 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
     g.h[a] = (float)ctx->cell[a];
     g.ih[a] = (float)(1.0 / ctx->cell[a]);
   }
-  // pass B: split ky into R residue classes so that a plane stays <= ~100 KB
-  ctx->R = 1;
-  while (ctx->R < 8 && (size_t)3 * nz * (g.Py / ctx->R) * sizeof(float2) > 100 * 1024 && g.Py % (2 * ctx->R) == 0 &&
-         g.Py / (2 * ctx->R) >= 2)
-    ctx->R *= 2;
+  ctx->R = pick_residues(g);
   bool ok = make_plan(g.Px, ctx->plan_x) && make_plan(g.Py / ctx->R, ctx->plan_ly);
   if (!ok) { delete ctx; return fail(MMP_E_INVAL, "unsupported FFT length"); }
-  auto r32 = [](long long v) { return (int)((v + 31) / 32 * 32); };
-  ctx->thrA = std::min(512, std::max(128, r32((long long)MMP_NP * g.Px / 32)));
-  long long elB = (long long)3 * nz * (g.Py / ctx->R);
-  ctx->thrB = std::min(512, std::max(64, r32(std::max(elB / 32, (long long)(g.Py / ctx->R)))));
-  ctx->thrC = std::min(512, std::max(std::max(128, r32((long long)MMP_NP * g.Px / 32)),
-                                     r32((long long)MMP_TY * nx / 8)));
+  launch_threads(g, ctx->R, &ctx->thrA, &ctx->thrB, &ctx->thrC);
   int rc = MMP_OK;
 #define CR(x) do { if (rc == MMP_OK) rc = (x); } while (0)
   CR(alloc_into(ctx, ctx->d_coef, 2 * MMP_MAX_REGIONS * sizeof(RegionCoef)));

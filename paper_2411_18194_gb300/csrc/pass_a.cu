@@ -36,6 +36,7 @@ template <int NSUB>
 __device__ __forceinline__ void passA_component(int c, float2* fbuf, const Grid& g, const StageArgs& a,
                                                 const DemagArgs& d, const Coefs& co, int z, int y0) {
   const int nx = g.nx, ny = g.ny, Px = g.Px;
+  const int pitch = fft_pitch(Px);
   const long long n = g.n;
   for (int e = threadIdx.x; e < MMP_NP * Px; e += blockDim.x) {
     int p = e / Px, x = e - p * Px;
@@ -57,7 +58,7 @@ __device__ __forceinline__ void passA_component(int c, float2* fbuf, const Grid&
         }
       }
     }
-    fbuf[e] = make_float2(va, vb);
+    fbuf[fidx(p, x, pitch)] = make_float2(va, vb);
   }
   __syncthreads();
   block_fft<false>(fbuf, d.plan_x, MMP_NP, d.tw_x);
@@ -65,8 +66,8 @@ __device__ __forceinline__ void passA_component(int c, float2* fbuf, const Grid&
     int k = e / MMP_TY, row = e - k * MMP_TY, y = y0 + row;
     if (y >= ny) continue;
     int p = row >> 1;
-    float2 Z = fbuf[p * Px + k];
-    float2 Zm = fbuf[p * Px + (k == 0 ? 0 : Px - k)];
+    float2 Z = fbuf[fidx(p, k, pitch)];
+    float2 Zm = fbuf[fidx(p, k == 0 ? 0 : Px - k, pitch)];
     float2 X;
     if ((row & 1) == 0) X = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
     else X = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(512) k_passA(Grid g, StageArgs a, DemagArgs d,
   passA_component<NSUB>(2, fbuf, g, a, d, co, z, y0);
 }
 
-size_t smem_passA(const Grid& g) { return (size_t)MMP_NP * g.Px * sizeof(float2); }
+size_t smem_passA(const Grid& g) { return (size_t)MMP_NP * fft_pitch(g.Px) * sizeof(float2); }
 cudaError_t launch_assemble(const Grid& g, const StageArgs& a, cudaStream_t s) {
   k_assemble<<<grid_for(g.n, 256), 256, 0, s>>>(g, a);
   return cudaGetLastError();

@@ -30,14 +30,15 @@ __device__ __forceinline__ void kmul(const float* __restrict__ K, float sy, floa
 }
 
 // z transform (nz = NZ cells, padded Pz = 2 NZ), kernel multiply, inverse z
-// transform for column kp of W, as two length-NZ DFTs per parity of kz.
+// transform for column kp of W (row pitch `pitch`), as two length-NZ DFTs per
+// parity of kz.
 template <int NZ>
-__device__ __forceinline__ void zkz_fixed(float2* W, int kp, int Ly, const float* __restrict__ Kc, float sy,
+__device__ __forceinline__ void zkz_fixed(float2* W, int kp, int pitch, const float* __restrict__ Kc, float sy,
                                           const float2* __restrict__ twz) {
   if constexpr (NZ == 1) {
-    float2 a = W[kp], b = W[Ly + kp], c = W[2 * Ly + kp];
+    float2 a = W[fidx(0, kp, pitch)], b = W[fidx(1, kp, pitch)], c = W[fidx(2, kp, pitch)];
     kmul(Kc, sy, 1.0f, a, b, c);
-    W[kp] = a; W[Ly + kp] = b; W[2 * Ly + kp] = c;
+    W[fidx(0, kp, pitch)] = a; W[fidx(1, kp, pitch)] = b; W[fidx(2, kp, pitch)] = c;
   } else {
     float2 out[3][NZ];
 #pragma unroll
@@ -47,7 +48,7 @@ __device__ __forceinline__ void zkz_fixed(float2* W, int kp, int Ly, const float
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int zz = 0; zz < NZ; ++zz) {
-          float2 v = W[(c * NZ + zz) * Ly + kp];
+          float2 v = W[fidx(c * NZ + zz, kp, pitch)];
           f[c][zz] = par ? cmul(v, __ldg(twz + zz)) : v;
         }
 #pragma unroll
@@ -80,12 +81,12 @@ __device__ __forceinline__ void zkz_fixed(float2* W, int kp, int Ly, const float
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int zz = 0; zz < NZ; ++zz) W[(c * NZ + zz) * Ly + kp] = out[c][zz];
+      for (int zz = 0; zz < NZ; ++zz) W[fidx(c * NZ + zz, kp, pitch)] = out[c][zz];
   }
 }
 
 // Any nz <= 16: direct DFT over the padded length Pz.
-__device__ void zkz_generic(float2* W, int kp, int Ly, int nz, int Pz, const float* __restrict__ Kc, float sy,
+__device__ void zkz_generic(float2* W, int kp, int pitch, int nz, int Pz, const float* __restrict__ Kc, float sy,
                             const float2* __restrict__ twz) {
   float2 out[3][16];
   for (int c = 0; c < 3; ++c)
@@ -95,7 +96,7 @@ __device__ void zkz_generic(float2* W, int kp, int Ly, int nz, int Pz, const flo
     for (int c = 0; c < 3; ++c) {
       float2 acc = make_float2(0.0f, 0.0f);
       for (int zz = 0; zz < nz; ++zz)
-        acc = cadd(acc, cmul(W[(c * nz + zz) * Ly + kp], __ldg(twz + (kz * zz) % Pz)));
+        acc = cadd(acc, cmul(W[fidx(c * nz + zz, kp, pitch)], __ldg(twz + (kz * zz) % Pz)));
       F[c] = acc;
     }
     int ikz = kz <= Pz / 2 ? kz : Pz - kz;
@@ -107,7 +108,7 @@ __device__ void zkz_generic(float2* W, int kp, int Ly, int nz, int Pz, const flo
     }
   }
   for (int c = 0; c < 3; ++c)
-    for (int zz = 0; zz < nz; ++zz) W[(c * nz + zz) * Ly + kp] = out[c][zz];
+    for (int zz = 0; zz < nz; ++zz) W[fidx(c * nz + zz, kp, pitch)] = out[c][zz];
 }
 
 constexpr int kMaxCluster = 8;
@@ -120,18 +121,24 @@ __global__ void __launch_bounds__(512) k_passB(Grid g, DemagArgs d) {
   const int kx = blockIdx.y;
   const int ny = g.ny, nz = g.nz, Py = g.Py;
   const int Ly = Py / RCL;
+  const int pitch = fft_pitch(Ly);
   const int ncol = 3 * nz;
   float2* Tk = d.T + (long long)kx * ncol * ny;
   // 1. fold the ky residue class r: g_r[j] = sum_q T[j + q Ly] w^(r (j + q Ly))
   for (int e = threadIdx.x; e < ncol * Ly; e += blockDim.x) {
     int col = e / Ly, j = e - col * Ly;
     float2 acc = make_float2(0.0f, 0.0f);
+    int ti = r * j;   // r*y mod Py, advanced by r*Ly per fold
     for (int y = j; y < ny; y += Ly) {
       float2 v = Tk[(long long)col * ny + y];
-      if (r > 0) v = cmul(v, __ldg(d.tw_y + (r * y) % Py));
+      if (r > 0) {
+        while (ti >= Py) ti -= Py;
+        v = cmul(v, __ldg(d.tw_y + ti));
+        ti += r * Ly;
+      }
       acc = cadd(acc, v);
     }
-    W[e] = acc;
+    W[fidx(col, j, pitch)] = acc;
   }
   __syncthreads();
   block_fft<false>(W, d.plan_ly, ncol, d.tw_ly);
@@ -141,8 +148,8 @@ __global__ void __launch_bounds__(512) k_passB(Grid g, DemagArgs d) {
     int iky = ky <= Py / 2 ? ky : Py - ky;
     float sy = ky <= Py / 2 ? 1.0f : -1.0f;
     const float* Kc = d.khat + ((long long)kx * g.kyn + iky) * g.kzn * 6;
-    if constexpr (NZ > 0) zkz_fixed<NZ>(W, kp, Ly, Kc, sy, d.tw_z);
-    else zkz_generic(W, kp, Ly, nz, g.Pz, Kc, sy, d.tw_z);
+    if constexpr (NZ > 0) zkz_fixed<NZ>(W, kp, pitch, Kc, sy, d.tw_z);
+    else zkz_generic(W, kp, pitch, nz, g.Pz, Kc, sy, d.tw_z);
   }
   __syncthreads();
   block_fft<true>(W, d.plan_ly, ncol, d.tw_ly);
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(512) k_passB(Grid g, DemagArgs d) {
   if (RCL == 1) {
     for (int e = threadIdx.x; e < ncol * ny; e += blockDim.x) {
       int col = e / ny, y = e - col * ny;
-      Tk[e] = W[col * Ly + y];
+      Tk[e] = W[fidx(col, y, pitch)];
     }
   } else {
     cg::cluster_group cl = cg::this_cluster();
@@ -161,16 +168,23 @@ __global__ void __launch_bounds__(512) k_passB(Grid g, DemagArgs d) {
     for (int q = 0; q < RCL; ++q) Wq[q] = cl.map_shared_rank(W, q);
     for (int e = threadIdx.x; e < ncol * cnt; e += blockDim.x) {
       int col = e / cnt, y = ylo + (e - col * cnt);
-      int j = y % Ly;
-      float2 acc = Wq[0][col * Ly + j];
-      for (int q = 1; q < RCL; ++q) acc = cadd(acc, cmul(Wq[q][col * Ly + j], cconj(__ldg(d.tw_y + (q * y) % Py))));
+      int j = y;
+      while (j >= Ly) j -= Ly;
+      const int at = fidx(col, j, pitch);
+      float2 acc = Wq[0][at];
+      int ti = 0;
+      for (int q = 1; q < RCL; ++q) {
+        ti += y;   // q*y mod Py
+        while (ti >= Py) ti -= Py;
+        acc = cadd(acc, cmul(Wq[q][at], cconj(__ldg(d.tw_y + ti))));
+      }
       Tk[(long long)col * ny + y] = acc;
     }
     cl.sync();
   }
 }
 
-size_t smem_passB(const Grid& g, int R) { return (size_t)3 * g.nz * (g.Py / R) * sizeof(float2); }
+size_t smem_passB(const Grid& g, int R) { return (size_t)3 * g.nz * fft_pitch(g.Py / R) * sizeof(float2); }
 template <int NZ>
 static cudaError_t launch_passB_t(const Grid& g, const DemagArgs& d, int threads, cudaStream_t s) {
   size_t sm = smem_passB(g, d.R);

@@ -1,0 +1,202 @@
+"""Parity of DP45 time integration on the CUDA path with the FP64 oracle,
+checkpoint/resume, relax, and the non-finite rollback."""
+import numpy as np
+import pytest
+
+from inputs import MU0, config_c1, config_c2, config_c3, config_small, random_unit_vectors
+from gpu_util import field_tolerance, make_magnet, gpu_eval, oracle_eval
+
+pytestmark = pytest.mark.gpu
+
+
+def _get_m(mag, p, s=0):
+    import torch
+    nx, ny, nz = p.shape
+    out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    mag.get_m(s, out)
+    return out.cpu().numpy()
+
+
+def test_c1_trajectory_and_per_eval_parity():
+    """64x64x1 ferromagnet, 2000 fixed DP45 steps at dt = 1e-13 s.
+
+    Per-evaluation field checks on the GPU-evolved states (~evals 0, 1000,
+    6000, 12000).  Trajectory: from a random state at alpha = 0.02 the
+    dynamics is chaotic, so the oracle itself is run twice (m0 and m0
+    perturbed at the 1e-7 level, the FP32 rounding scale); their spread
+    e-folds every ~40 steps and is O(1) after 2000 steps, so no
+    implementation can meet max|dm| <= 1e-4 there.  The bar is asserted at
+    every checkpoint where the oracle's own spread is below 1e-5 (up to
+    ~step 100); at every checkpoint the GPU's deviation must stay within the
+    chaotic amplification of FP32-sized errors: max|dm| <= 10 x spread + 1e-4."""
+    from oracle.dp45 import Oracle, State
+    w = config_c1()
+    p = w.problem
+    mag = make_magnet(p, w.m0)
+    mag.set_solver(adaptive=False, dt=w.dt)
+    checks = (0, 50, 100, 167, 200, 300, 400, 600, 800, 1000, 1500, 2000)
+    field_at = (0, 167, 1000, 2000)
+    gpu_m = {}
+    done = 0
+    for target in checks:
+        if target > done:
+            mag.step(target - done)
+            done = target
+        m = _get_m(mag, p)
+        gpu_m[target] = m
+        if target in field_at:
+            Bg, _ = gpu_eval(mag, p)
+            Bo, _ = oracle_eval(p, [m])
+            err = np.abs(Bg[0] - Bo[0])
+            assert np.all(err <= field_tolerance(p, Bo[0])), (target, err.max())
+    assert mag.time()["evals"] >= 1 + 6 * 2000
+    mag.close()
+    ref, pert = {0: w.m0[0].astype(np.float64)}, {}
+    o = Oracle(p)
+    o.run_fixed(State(w.m0), w.dt, w.steps,
+                callback=lambda n, st: ref.__setitem__(n, st.ms[0].copy()) if n in checks else None)
+    rng = np.random.default_rng(0)
+    m_pert = w.m0[0].astype(np.float64) * (1 + 1e-7 * rng.standard_normal(w.m0[0].shape))
+    pert[0] = m_pert
+    Oracle(p, noct=o.noct).run_fixed(State([m_pert]), w.dt, w.steps,
+                                     callback=lambda n, st: pert.__setitem__(n, st.ms[0].copy())
+                                     if n in checks else None)
+    asserted = []
+    for n in checks:
+        dm = np.abs(gpu_m[n] - ref[n]).max()
+        sens = np.abs(pert[n] - ref[n]).max()
+        print("C1 step %5d: max|dm| GPU-oracle %.3e   oracle self-sensitivity %.3e" % (n, dm, sens))
+        if sens <= 1e-5:
+            assert dm <= 1e-4, (n, dm, sens)
+            asserted.append(n)
+        assert dm <= 10.0 * sens + 1e-4, (n, dm, sens)
+    assert max(asserted) >= 100
+
+
+def test_adaptive_run_matches_oracle():
+    from oracle.dp45 import Oracle, State
+    w = config_small((24, 20, 2), (2e-9, 2e-9, 1e-9), 51)
+    p = w.problem
+    mag = make_magnet(p, w.m0)
+    mag.set_solver(adaptive=True, dt=1e-15, tol=1e-5)
+    mag.run(20e-12)
+    info = mag.time()
+    m_gpu = _get_m(mag, p)
+    o = Oracle(p)
+    st, stats = o.run_adaptive(State(w.m0), 1e-15, 1e-5, 20e-12)
+    assert info["t"] == pytest.approx(20e-12, rel=1e-12)
+    assert abs(info["steps"] - stats["accepted"]) <= max(2, 0.05 * stats["accepted"])
+    assert np.abs(m_gpu - st.ms[0]).max() <= 1e-4
+    mag.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = config_small((20, 12, 2), (2e-9, 2e-9, 1e-9), 61)
+    p = w.problem
+    mag = make_magnet(p, w.m0)
+    mag.set_solver(adaptive=True, dt=1e-15, tol=1e-5)
+    mag.step(10)
+    blob = mag.get_state()
+    mag.step(15)
+    a = _get_m(mag, p)
+    ta = mag.time()
+    mag.set_state(blob)
+    mag.step(15)
+    b = _get_m(mag, p)
+    tb = mag.time()
+    assert np.array_equal(a, b)
+    assert ta["t"] == tb["t"] and ta["steps"] == tb["steps"]
+    mag.close()
+
+
+def test_relax_reaches_torque_tolerance():
+    w = config_small((32, 24, 1), (4e-9, 4e-9, 2e-9), 71, terms=("DEMAG", "EXCH", "ZEEMAN"))
+    p = w.problem
+    p.set("ALPHA", 0.5).set("B_EXT", (0.0, 0.0, 0.05))
+    mag = make_magnet(p, w.m0)
+    mag.set_solver(adaptive=True, dt=1e-14, tol=1e-5)
+    mag.relax(torque_tol=1e-4, max_time=10e-9, timeout_s=60.0)
+    m = _get_m(mag, p)
+    Bg, _ = gpu_eval(mag, p)
+    mxB = np.cross(m.reshape(3, -1).T, Bg[0].reshape(3, -1).T)
+    assert np.linalg.norm(mxB, axis=1).max() <= 1.5e-4
+    assert mag.time()["t"] < 10e-9
+    mag.close()
+
+
+def test_nonfinite_state_is_reported_and_rolled_back():
+    import paper_2411_18194_gb300 as pkg
+    w = config_small((8, 8, 1), (2e-9, 2e-9, 2e-9), 81)
+    p = w.problem
+    m = w.m0[0].copy()
+    m[0, 0, 3, 3] = np.nan
+    mag = make_magnet(p, [m])
+    mag.set_solver(adaptive=True, dt=1e-15, tol=1e-5)
+    with pytest.raises(pkg.MmpError) as e:
+        mag.step(1)
+    assert e.value.status == -4
+    after = _get_m(mag, p)
+    assert np.array_equal(np.isnan(after), np.isnan(m))
+    assert np.array_equal(after[~np.isnan(after)], m[~np.isnan(m)])
+    mag.close()
+
+
+def test_two_sublattice_magnetoelastic_trajectory():
+    """Short fixed-dt run of the antiferromagnet + magnetoelastic + elastic
+    workload on a reduced grid (same materials, dt = 5e-15 s)."""
+    from oracle.dp45 import Oracle, State
+    w = config_c3()
+    p = w.problem
+    p.shape = (48, 24, 1)
+    p.regions = np.zeros((1, 24, 48), dtype=np.uint8)
+    from inputs import noisy_axis_vectors
+    m0 = [noisy_axis_vectors(w.seed, p.shape, (1.0, 0, 0), 1.0, sub=0),
+          noisy_axis_vectors(w.seed, p.shape, (-1.0, 0, 0), 1.0, sub=1)]
+    z = np.zeros((3, 1, 24, 48), dtype=np.float32)
+    mag = make_magnet(p, m0, z, z)
+    mag.set_solver(adaptive=False, dt=w.dt)
+    nsteps = 200
+    mag.step(nsteps)
+    mg = [_get_m(mag, p, s) for s in range(2)]
+    import torch
+    ug = torch.empty((3, 1, 24, 48), dtype=torch.float32, device="cuda")
+    vg = torch.empty_like(ug)
+    mag.get_elastic(ug, vg)
+    o = Oracle(p)
+    st = o.run_fixed(State(m0, z, z), w.dt, nsteps)
+    for s in range(2):
+        assert np.abs(mg[s] - st.ms[s]).max() <= 1e-4
+    du = np.abs(ug.cpu().numpy() - st.u).max() / max(np.abs(st.u).max(), 1e-30)
+    assert np.abs(st.u).max() > 0 and du <= 1e-3
+    mag.close()
+
+
+def test_c2_full_size_sampled_parity():
+    """The large ferromagnet at full size (1024x1024x8) in the launch
+    configuration the benchmark times: B_eff at sampled cells against the
+    oracle's direct sum of the demag definition plus its local terms."""
+    from oracle import demag, fields
+    w = config_c2()
+    p = w.problem
+    nx, ny, nz = p.shape
+    mag = make_magnet(p, w.m0)
+    Bg, _ = gpu_eval(mag, p)
+    mag.close()
+    m = w.m0[0].astype(np.float64)
+    noct = demag.tensor_octant(p.shape, p.cell)
+    P = fields.cell_params(p)
+    local = sum(fields.effective_fields(
+        p.__class__(p.shape, p.cell, 1, frozenset(p.terms - {"DEMAG"}), p.regions, p.scal, p.vec, p.glob),
+        [m], P=P))
+    rng = np.random.default_rng(3)
+    picks = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny - 1, 3), (nx - 1, 0, 4), (512, 512, 0),
+             (511, 3, 7), (1, 1000, 2)]
+    picks += [tuple(int(v) for v in (rng.integers(nx), rng.integers(ny), rng.integers(nz))) for _ in range(17)]
+    cells = [x + nx * (y + ny * z) for x, y, z in picks]
+    M = P["MS"][0] * m
+    Bd = demag.demag_direct(p.shape, p.cell, M, noct=noct, cells=cells)
+    bar = 1e-5 * MU0 * 1.1e6
+    for (x, y, z), bd in zip(picks, Bd.T):
+        ref = bd + local[:, z, y, x]
+        got = Bg[0][:, z, y, x]
+        assert np.abs(got - ref).max() <= bar, ((x, y, z), got, ref)
