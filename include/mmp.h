@@ -195,6 +195,29 @@ enum mmp_kernel {
 int mmp_profile(mmp_ctx* ctx, int enable);
 int mmp_profile_read(mmp_ctx* ctx, int kernel, long long* launches, double* total_ms);
 
+/* Demagnetising field without any device allocation (the paper has no
+ * counterpart; it exists for callers that cannot call cudaMalloc, e.g. code
+ * whose device memory is owned by a host framework, or a loop that must not
+ * allocate once running).
+ *   B = -mu0 N * M on an nx*ny*nz grid of cx*cy*cz cells (same tensor, FFT
+ *   passes and kernels as the context path), M in A/m and B in tesla, both
+ *   caller-owned device float32 [3][nz][ny][nx]; work is enqueued on
+ *   `stream` (cudaStream_t, NULL = legacy default stream).
+ * All working memory is one file-scope static device array of
+ * MMP_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading the library holds
+ * until exit.  Grids needing more (roughly above 2e5 cells) are rejected with
+ * MMP_E_INVAL and a message giving the size.  The first call on a device,
+ * and the first call after the geometry (extents or cell size) changes,
+ * sets the array up: it looks up the array's device address, copies tables
+ * from the host, builds the demag kernel and synchronises the stream -- make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (the kernel of the last geometry); calls
+ * that overlap on the GPU, or run concurrently on two host threads with
+ * different geometries, race on it. */
+#define MMP_NOALLOC_SCRATCH_BYTES (32 * 1024 * 1024)
+int mmp_demag_noalloc(int nx, int ny, int nz, double cx, double cy, double cz, const float* M, float* B,
+                      void* stream);
+
 /* Wait for all work of the context. */
 int mmp_sync(mmp_ctx* ctx);
 

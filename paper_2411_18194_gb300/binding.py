@@ -55,6 +55,8 @@ _SIGS = {
     "mmp_set_state": ([_c.c_void_p, _c.c_void_p, _c.c_size_t], _c.c_int),
     "mmp_sync": ([_c.c_void_p], _c.c_int),
     "mmp_profile": ([_c.c_void_p, _c.c_int], _c.c_int),
+    "mmp_demag_noalloc": ([_c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double, _c.c_void_p,
+                           _c.c_void_p, _c.c_void_p], _c.c_int),
     "mmp_profile_read": ([_c.c_void_p, _c.c_int, _c.POINTER(_c.c_longlong), _c.POINTER(_c.c_double)],
                          _c.c_int),
 }
@@ -127,6 +129,20 @@ class _TorchAllocator:
 
     def _free(self, ptr, user):
         self._torch.cuda.caching_allocator_delete(ptr)
+
+
+def demag_noalloc(shape, cell, M, B, stream=None):
+    """B = demag field of M (device float32 tensors [3][nz][ny][nx]) through
+    mmp_demag_noalloc: no device allocation, static scratch inside the
+    library (see include/mmp.h for its size limit and sharing rules)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    nx, ny, nz = (int(v) for v in shape)
+    cx, cy, cz = (float(c) for c in cell)
+    _check(library().mmp_demag_noalloc(nx, ny, nz, cx, cy, cz, _ptr(M), _ptr(B), ctypes.c_void_p(handle)))
+    return B
 
 
 class Magnet:

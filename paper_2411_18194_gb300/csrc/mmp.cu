@@ -550,6 +550,11 @@ int advance(mmp_ctx* ctx, long long nsteps, double until, int relax, double torq
 
 }  // namespace
 
+namespace mmp {
+// Record an error message for mmp_last_error() from another translation unit.
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace mmp
+
 // ============================================================== C-ABI =====
 extern "C" {
 
