@@ -98,19 +98,25 @@ class ClockSampler:
         return out
 
 
-def kernel_bytes(g, nk_avg):
-    """Algorithmic DRAM bytes per launch of each pass (per eval), see the design doc."""
+def kernel_bytes(g, nk_avg, nparts=1, nsub=1, mel=False):
+    """Algorithmic DRAM bytes per launch of each pass (per eval), see the design doc:
+    each array that a pass must read or write, once."""
     nx, ny, nz = g["shape"]
     n = nx * ny * nz
     kxn = g["Px"] // 2 + 1
     kyn = g["Py"] // 2 + 1
     kzn = g["Pz"] // 2 + 1
+    krow = (6 * kzn + 3) // 4 * 4
     spec = 3 * kxn * ny * nz * 8            # x-transformed spectrum, complex64
-    khat = kxn * kyn * kzn * 6 * 4          # kernel octant, float32
+    khat = kxn * kyn * krow * 4             # kernel octant rows, float32
+    part = 12 * n                            # one 3-vector field, float32
     return {
-        "pass_a": 12 * n * (1 + nk_avg) + 12 * n + spec,   # read m, k_j; write stage; write spectrum
-        "pass_b": 2 * spec + khat,                          # spectrum in/out + kernel octant
-        "field": spec + 12 * n + 12 * n,                    # spectrum in, stage m in, k out
+        # read y and the n_k earlier stages, write the stage, write the spectrum
+        "pass_a": part * nparts * (1 + nk_avg) + part * nparts + spec,
+        # spectrum in and out, kernel octant in
+        "pass_b": 2 * spec + khat,
+        # spectrum in, stage m in, k out (+ strain in)
+        "field": spec + part * nsub * 2 + (24 * n if mel else 0),
     }
 
 
@@ -135,6 +141,20 @@ def traffic_from_profile(kernel):
         return rec["dram_bytes_per_launch"] if sha == rec["source_sha"] else None
     except Exception:
         return None
+
+
+def reduce_over_ranks(maxes, sums, device):
+    """Whole-job numbers of independent replicas: the max over ranks of each
+    value in `maxes` (times) and the sum of each value in `sums` (work,
+    throughputs).  Identity when not running distributed."""
+    import torch
+    mx = torch.tensor([float(v) for v in maxes], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(v) for v in sums], dtype=torch.float64, device=device)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.tolist(), sm.tolist()
 
 
 def cpu_baseline(seconds=15.0):
@@ -203,6 +223,16 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+WORKLOADS = {
+    "c2": "ferromagnet 1024x1024x8 cells of 2x2x1 nm, Ms 1.1e6, A 1.6e-11, Ku 8e5 (z), iDMI 3e-3, "
+          "alpha 0.1; demag+exchange+anisotropy+iDMI; adaptive DP45 tol 1e-5 from dt 1e-14",
+    "c1": "ferromagnet 64x64x1 cells of 4 nm, Ms 8e5, A 1.3e-11, alpha 0.02, B = 10 mT along z; "
+          "demag+exchange+Zeeman; fixed DP45 dt 1e-13",
+    "c3": "two-sublattice antiferromagnet 1024x256x1 cells of 2 nm with magnetoelastic coupling and "
+          "elastodynamics (biaxial anisotropy, A0 -4e-11, A12 -1e-12); fixed DP45 dt 5e-15",
+}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -214,15 +244,18 @@ def run_gpu(args):
     else:
         torch.cuda.set_device(0)
     import paper_2411_18194_gb300 as pkg
-    from inputs import config_c2
-    w = config_c2()
+    from inputs import config_c1, config_c2, config_c3
+    w = {"c1": config_c1, "c2": config_c2, "c3": config_c3}[args.workload]()
     p = w.problem
     nx, ny, nz = p.shape
     ncell = nx * ny * nz * p.n_sub
     mag = pkg.Magnet.from_problem(p)
+    for s_, m_ in enumerate(w.m0):
+        mag.set_m(s_, torch.from_numpy(m_).cuda())
+    if w.u0 is not None:
+        mag.set_elastic(torch.from_numpy(w.u0).cuda(), torch.from_numpy(w.v0).cuda())
     m0 = torch.from_numpy(w.m0[0]).cuda()
-    mag.set_m(0, m0)
-    mag.set_solver(adaptive=True, dt=w.dt, tol=w.tol, dt_min=1e-18, dt_max=1e-11)
+    mag.set_solver(adaptive=w.adaptive, dt=w.dt, tol=w.tol, dt_min=1e-18, dt_max=1e-11)
 
     def barrier():
         if ws > 1:
@@ -253,28 +286,25 @@ def run_gpu(args):
     prof = mag.profile_read()
     mag.profile(False)
     launches = sum(v[0] for v in prof.values())
-    t_rank = torch.tensor([ms], device="cuda")
-    ev_rank = torch.tensor([float(evals * ncell)], device="cuda")
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ev_rank, op=dist.ReduceOp.SUM)
-    t_max = t_rank.item()
-    value = ev_rank.item() / (t_max * 1e-3) / 1e6
+    (t_max,), (all_evals,) = reduce_over_ranks([ms], [evals * ncell], "cuda")
+    value = all_evals / (t_max * 1e-3) / 1e6
 
     # roofline of the dominant kernel
     g = geometry(p.shape)
     nk_avg = (0 + 1 + 2 + 3 + 4 + 5 + 5) / 7.0   # k vectors read by stage assembly per eval (a72 = 0)
-    kb = kernel_bytes(g, nk_avg)
-    dom = max((k for k in prof if k in kb), key=lambda k: prof[k][1])
+    kb = kernel_bytes(g, nk_avg, nparts=p.n_sub + (2 if "ELASTIC" in p.terms else 0), nsub=p.n_sub,
+                      mel="MEL" in p.terms)
+    dom = max((k for k in prof if k in kb) if any(k in kb for k in prof) else prof,
+              key=lambda k: prof[k][1])
     n_l, tot_ms = prof[dom]
     avg_s = tot_ms / n_l * 1e-3
     peak, src = peaks()
-    achieved = kb[dom] / avg_s / 1e9
+    achieved = kb.get(dom, 0) / avg_s / 1e9
     share = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
 
     # end to end through the public API with host buffers: per step the state
-    # is copied in from pinned host memory and read back.
+    # (magnetisation of sublattice 0) is copied in from pinned host memory and
+    # read back.
     host_in = torch.from_numpy(w.m0[0]).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     mag.get_m(0, host_in)
@@ -291,10 +321,7 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - t0
     e2e_evals = mag.time()["evals"] - e1
     e2e_value = e2e_evals * ncell / e2e_s / 1e6
-    e2e_t = torch.tensor([e2e_value], device="cuda")
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.SUM)
+    _, (e2e_all,) = reduce_over_ranks([], [e2e_value], "cuda")
     nbytes = 12 * nx * ny * nz
 
     if rank == 0:
@@ -303,21 +330,21 @@ def run_gpu(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random m0)",
-            "config": {"workload": "ferromagnet 1024x1024x8 cells of 2x2x1 nm, Ms 1.1e6, A 1.6e-11, "
-                                   "Ku 8e5 (z), iDMI 3e-3, alpha 0.1; demag+exchange+anisotropy+iDMI; "
-                                   "adaptive DP45 tol 1e-5 from dt 1e-14",
+            "config": {"workload": WORKLOADS[args.workload],
                        "cells": nx * ny * nz, "sublattices": p.n_sub, "parallelism": "replicas",
                        "step": "one DP45 attempt (6 field evaluations + error readback)",
                        "evals": evals, "accepted": tinfo["steps"], "rejected": tinfo["rejected"],
                        "sim_time_s": tinfo["t"], "dt_s": tinfo["dt"],
-                       "l2": "inputs larger than L2 (state + stages + spectra ~1.3 GB)"},
+                       "l2": ("inputs larger than L2 (state + stages + spectra ~1.3 GB)" if args.workload == "c2"
+                              else "working set fits in L2; no flush between steps")},
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic_from_profile(dom), "bytes_per_launch": kb[dom],
+                         "traffic": traffic_from_profile(dom) if args.workload == "c2" else None,
+                         "bytes_per_launch": kb.get(dom),
                          "avg_launch_ms": avg_s * 1e3, "launches": n_l},
             "kernel_share": share,
-            "cpu_baseline": cpu_baseline() if not args.no_cpu_baseline else None,
-            "e2e": {"value": e2e_t.item(), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "cpu_baseline": cpu_baseline() if not args.no_cpu_baseline and args.workload == "c2" else None,
+            "e2e": {"value": e2e_all, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clk,
@@ -354,6 +381,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-evals", type=int, default=0)
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"],
+                    help="c2 (default, the benchmark line); c1, c3 for the other workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.profile_evals:

@@ -4,8 +4,7 @@
 #include <stdint.h>
 
 #define MMP_MAX_REGIONS 256
-#define MMP_TY 8              // rows (y) per tile of the x-FFT passes
-#define MMP_NP (MMP_TY / 2)   // row pairs per tile
+#define MMP_TY 8              // largest number of rows (y) per tile of the x-FFT passes
 
 namespace mmp {
 

@@ -144,14 +144,15 @@ struct PassCap { static constexpr int B = (R == 3) ? CAP / 3 : CAP / R; };
 // held in shared memory with the padded layout above.  Ns (the product of
 // the radices already applied) is a power of two for every pass of the
 // plans used here (the one radix-3 pass comes last on lengths 3*2^a).
+// Twiddles of this pass: tw[(r-1) Ns + k] = w_{Ns R}^{r k} (pass-ordered
+// table, see pass_twiddles() on the host), so lanes with consecutive k read
+// consecutive words.
 // Requires L*nbatch <= (CAP/R)*R*blockDim.x (checked by the host).
 template <int R, bool INV, int CAP>
-__device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, int Ns,
-                                              const float2* __restrict__ tw) {
+__device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, int Ns, const float2* tw) {
   constexpr int MAXB = PassCap<R, CAP>::B;
   const int nbf = L / R;
   const int total = nbf * nbatch;
-  const int tstride = L / (Ns * R);
   const int pitch = fft_pitch(L);
   // t = b / nbf without an integer division: (b + 1/2) / nbf is at least
   // 1/(2 nbf) away from an integer and b, nbf < 2^15, so the FP32 quotient
@@ -175,11 +176,12 @@ __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, i
       int t = (int)(((float)b + 0.5f) * rnbf), j = b - t * nbf;
       int k = j & (Ns - 1);
       if (Ns > 1) {
+        const float2* w = tw + k;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(tw + r * k * tstride);
-          if (INV) w.y = -w.y;
-          v[i][r] = cmul(v[i][r], w);
+          float2 wr = w[(r - 1) * Ns];
+          if (INV) wr.y = -wr.y;
+          v[i][r] = cmul(v[i][r], wr);
         }
       }
       dft<R, INV>(v[i]);
@@ -193,16 +195,26 @@ __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, i
 
 // Full transform of a batch in shared memory (natural order in and out).
 // Callers __syncthreads() before (data written) and may read right after.
+// `tw` is the pass-ordered twiddle table of the plan (L - 1 entries) in
+// shared or global memory.
 template <bool INV, int CAP = 32>
-__device__ __forceinline__ void block_fft(float2* data, const FftPlan p, int nbatch, const float2* __restrict__ tw) {
+__device__ __forceinline__ void block_fft(float2* data, const FftPlan p, int nbatch, const float2* tw) {
   int Ns = 1;
 #pragma unroll 1
-  for (int s = 0; s < p.n16; ++s) { stockham_pass<16, INV, CAP>(data, p.L, nbatch, Ns, tw); Ns *= 16; }
-  if (p.n8) { stockham_pass<8, INV, CAP>(data, p.L, nbatch, Ns, tw); Ns *= 8; }
-  if (p.n4) { stockham_pass<4, INV, CAP>(data, p.L, nbatch, Ns, tw); Ns *= 4; }
-  if (p.n2) { stockham_pass<2, INV, CAP>(data, p.L, nbatch, Ns, tw); Ns *= 2; }
+  for (int s = 0; s < p.n16; ++s) {
+    stockham_pass<16, INV, CAP>(data, p.L, nbatch, Ns, tw);
+    if (Ns > 1) tw += 15 * Ns;
+    Ns *= 16;
+  }
+  if (p.n8) { stockham_pass<8, INV, CAP>(data, p.L, nbatch, Ns, tw); if (Ns > 1) tw += 7 * Ns; Ns *= 8; }
+  if (p.n4) { stockham_pass<4, INV, CAP>(data, p.L, nbatch, Ns, tw); if (Ns > 1) tw += 3 * Ns; Ns *= 4; }
+  if (p.n2) { stockham_pass<2, INV, CAP>(data, p.L, nbatch, Ns, tw); if (Ns > 1) tw += Ns; Ns *= 2; }
 #pragma unroll 1
-  for (int s = 0; s < p.n3; ++s) { stockham_pass<3, INV, CAP>(data, p.L, nbatch, Ns, tw); Ns *= 3; }
+  for (int s = 0; s < p.n3; ++s) {
+    stockham_pass<3, INV, CAP>(data, p.L, nbatch, Ns, tw);
+    if (Ns > 1) tw += 2 * Ns;
+    Ns *= 3;
+  }
 }
 
 }  // namespace mmp

@@ -177,12 +177,12 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
 
 // One component of the inverse x transform of pass C: Hermitian-extended
 // row pairs from T, inverse FFT, the x < nx outputs into bd[c][row][x].
-__device__ __forceinline__ void inverse_x_component(int c, float2* fbuf, float* bd, const Grid& g,
-                                                    const DemagArgs& d, int z, int y0) {
+__device__ __forceinline__ void inverse_x_component(int c, float2* fbuf, const float2* tw, float* bd,
+                                                    const Grid& g, const DemagArgs& d, int z, int y0) {
   const int nx = g.nx, ny = g.ny, Px = g.Px;
   const int pitch = fft_pitch(Px);
-  for (int e = threadIdx.x; e < MMP_NP * Px; e += blockDim.x) {
-    int k = e / MMP_NP, p = e - k * MMP_NP;
+  for (int e = threadIdx.x; e < (g.ty >> 1) * Px; e += blockDim.x) {
+    int k = e / (g.ty >> 1), p = e - k * (g.ty >> 1);
     int kk = k <= Px / 2 ? k : Px - k;
     int ya = y0 + 2 * p, yb = ya + 1;
     const float2* Tc = d.T + (((long long)kk * 3 + c) * g.nz + z) * ny;
@@ -192,11 +192,11 @@ __device__ __forceinline__ void inverse_x_component(int c, float2* fbuf, float* 
     fbuf[fidx(p, k, pitch)] = make_float2(xa.x - xb.y, xa.y + xb.x);
   }
   __syncthreads();
-  block_fft<true>(fbuf, d.plan_x, MMP_NP, d.tw_x);
-  for (int e = threadIdx.x; e < MMP_TY * nx; e += blockDim.x) {
+  block_fft<true>(fbuf, d.plan_x, (g.ty >> 1), tw);
+  for (int e = threadIdx.x; e < g.ty * nx; e += blockDim.x) {
     int row = e / nx, x = e - row * nx;
     float2 v = fbuf[fidx(row >> 1, x, pitch)];
-    bd[(c * MMP_TY + row) * nx + x] = (row & 1) ? v.y : v.x;
+    bd[(c * g.ty + row) * nx + x] = (row & 1) ? v.y : v.x;
   }
   __syncthreads();
 }
@@ -205,17 +205,19 @@ template <int NSUB, bool DEMAG, bool UNI>
 __global__ void __launch_bounds__(512) k_field(Grid g, DemagArgs d, Coefs co, FieldArgs f) {
   extern __shared__ float smem[];
   const int nx = g.nx, ny = g.ny, Px = g.Px;
-  const int z = blockIdx.y, y0 = blockIdx.x * MMP_TY;
+  const int z = blockIdx.y, y0 = blockIdx.x * g.ty;
   float* bd = smem;                                                     // [3][TY][nx]
-  float2* fbuf = reinterpret_cast<float2*>(smem + ((3 * MMP_TY * nx + 3) & ~3));   // [NP][Px]
+  float2* fbuf = reinterpret_cast<float2*>(smem + ((3 * g.ty * nx + 3) & ~3));   // [NP][Px]
   if (DEMAG) {
-    inverse_x_component(0, fbuf, bd, g, d, z, y0);
-    inverse_x_component(1, fbuf, bd, g, d, z, y0);
-    inverse_x_component(2, fbuf, bd, g, d, z, y0);
+    float2* tw = fbuf + (g.ty >> 1) * fft_pitch(Px);
+    for (int i = threadIdx.x; i < Px; i += blockDim.x) tw[i] = __ldg(d.tw_x + i);
+    inverse_x_component(0, fbuf, tw, bd, g, d, z, y0);
+    inverse_x_component(1, fbuf, tw, bd, g, d, z, y0);
+    inverse_x_component(2, fbuf, tw, bd, g, d, z, y0);
   }
   float emax = 0.0f, tmax = 0.0f;
   const long long n = g.n;
-  for (int e = threadIdx.x; e < MMP_TY * nx; e += blockDim.x) {
+  for (int e = threadIdx.x; e < g.ty * nx; e += blockDim.x) {
     int row = e / nx, x = e - row * nx, y = y0 + row;
     if (y >= ny) continue;
     long long cell = x + (long long)nx * (y + (long long)ny * z);
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(512) k_field(Grid g, DemagArgs d, Coefs co, Fi
     float b3[3] = {0.0f, 0.0f, 0.0f};
     if (DEMAG) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) b3[c] = bd[(c * MMP_TY + row) * nx + x];
+      for (int c = 0; c < 3; ++c) b3[c] = bd[(c * g.ty + row) * nx + x];
     }
 #pragma unroll
     for (int s = 0; s < NSUB; ++s) {
@@ -257,12 +259,13 @@ __global__ void __launch_bounds__(512) k_field(Grid g, DemagArgs d, Coefs co, Fi
 
 size_t smem_field(const Grid& g, bool demag) {
   if (!demag) return 0;
-  return (size_t)((3 * MMP_TY * g.nx + 3) & ~3) * sizeof(float) + (size_t)MMP_NP * fft_pitch(g.Px) * sizeof(float2);
+  return (size_t)((3 * g.ty * g.nx + 3) & ~3) * sizeof(float) +
+         ((size_t)(g.ty >> 1) * fft_pitch(g.Px) + g.Px) * sizeof(float2);
 }
 
 cudaError_t launch_field(const Grid& g, const DemagArgs& d, const Coefs& c, const FieldArgs& f, int nsub,
                          bool demag, int threads, cudaStream_t s) {
-  dim3 grid((g.ny + MMP_TY - 1) / MMP_TY, g.nz);
+  dim3 grid((g.ny + g.ty - 1) / g.ty, g.nz);
   size_t sm = smem_field(g, demag);
   cudaError_t e;
 #define MMP_F(NS, DM, UN)                                               \

@@ -16,7 +16,8 @@ struct KernelBuild {
   double* buf0;        // FP64 scratch, 6 * max(extent products) doubles
   double* buf1;
   const double2* trig[3];   // (cos, sin)(2 pi t / P_a), device
-  float* out;          // [Px/2+1][Py/2+1][Pz/2+1][6]
+  float* out;          // [Px/2+1][Py/2+1][krow], row = (kz, 6 components) + padding
+  int krow;
 };
 cudaError_t build_kernel_spectrum(const KernelBuild& kb, cudaStream_t s);
 
@@ -27,6 +28,8 @@ struct Grid {
   int Px, Py, Pz;       // padded lengths (1 on axes with n = 1)
   int kxn;              // Px/2 + 1
   int kyn, kzn;         // Py/2 + 1, Pz/2 + 1
+  int krow;             // floats per (kx, ky) row of the kernel octant: 6 kzn rounded up to 4
+  int ty;               // rows (y) per tile of passes A and C: 2, 4 or 8 (row pairs = ty / 2)
   float h[3];           // cell size (m)
   float ih[3];          // 1 / h
 };
@@ -46,10 +49,10 @@ struct StageArgs {
 
 struct DemagArgs {
   float2* T;                 // spectrum [kxn][3][nz][ny] complex
-  const float* khat;         // kernel octant [kxn][kyn][kzn][6]
-  const float2* tw_x;        // Px roots (forward)
+  const float* khat;         // kernel octant [kxn][kyn][krow] (krow >= 6 kzn, 16-byte rows)
+  const float2* tw_x;        // pass-ordered twiddles of plan_x (Px entries)
   const float2* tw_y;        // Py roots
-  const float2* tw_ly;       // Ly = Py / R roots
+  const float2* tw_ly;       // pass-ordered twiddles of plan_ly (Ly = Py / R entries)
   const float2* tw_z;        // Pz roots
   FftPlan plan_x, plan_ly;
   int R;                     // residue classes of ky per cluster
@@ -96,6 +99,25 @@ cudaError_t launch_strain(const Grid& g, const ElasticArgs& e, int nsub, cudaStr
 cudaError_t launch_elastic_rhs(const Grid& g, const ElasticArgs& e, const Coefs& c, int nsub,
                                cudaStream_t s);
 cudaError_t launch_normalize(float* m, long long n, cudaStream_t s);
+
+// Shared-memory carve-up of one pass-B CTA (bytes from the start).
+struct PassBSmem {
+  size_t twl, twf, twc, ks, total;
+};
+
+__host__ __device__ __forceinline__ PassBSmem passb_smem(int ny, int nz, int Py, int kzn, int R) {
+  const int Ly = Py / R;
+  const int cnt = (ny + R - 1) / R;
+  PassBSmem s;
+  size_t at = (size_t)3 * nz * fft_pitch(Ly) * sizeof(float2);
+  s.twl = at; at += (size_t)Ly * sizeof(float2);
+  s.twf = at; at += (size_t)Ly * sizeof(float2);
+  s.twc = at; at += (size_t)cnt * sizeof(float2);
+  at = (at + 15) & ~(size_t)15;   // 16-byte rows for cp.async
+  s.ks = at; at += (size_t)Ly * ((6 * kzn + 3) & ~3) * sizeof(float);
+  s.total = at;
+  return s;
+}
 
 // shared memory bytes of each pass (host side planning)
 size_t smem_passA(const Grid& g);

@@ -257,7 +257,7 @@ int build_khat(mmp_ctx* ctx) {
   if (!ctx->khat_dirty) return MMP_OK;
   const Grid& g = ctx->g;
   size_t nk = (size_t)g.kxn * g.kyn * g.kzn;
-  TRY(alloc_into(ctx, ctx->d_khat, nk * 6 * sizeof(float)));
+  TRY(alloc_into(ctx, ctx->d_khat, (size_t)g.kxn * g.kyn * g.krow * sizeof(float)));
   long long ext = std::max<long long>({(long long)g.nx * g.ny * g.nz, (long long)g.kxn * g.ny * g.nz,
                                        (long long)g.kxn * g.kyn * g.nz, (long long)nk});
   double* b0 = nullptr;
@@ -288,6 +288,7 @@ int build_khat(mmp_ctx* ctx) {
     kb.buf0 = b0;
     kb.buf1 = b1;
     kb.out = ctx->d_khat;
+    kb.krow = g.krow;
     rc = cuda_check(ctx, build_kernel_spectrum(kb, ctx->stream), "demag kernel build");
     if (rc == MMP_OK) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "demag kernel build (sync)");
   }
@@ -598,11 +599,14 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
   g.nx = nx; g.ny = ny; g.nz = nz; g.n = n;
   g.Px = nice_length(nx); g.Py = nice_length(ny); g.Pz = nice_length(nz);
   g.kxn = g.Px / 2 + 1; g.kyn = g.Py / 2 + 1; g.kzn = g.Pz / 2 + 1;
+  g.krow = (6 * g.kzn + 3) & ~3;
+  g.ty = pick_tile_rows(g.ny, g.nz);
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (float)ctx->cell[a];
     g.ih[a] = (float)(1.0 / ctx->cell[a]);
   }
   ctx->R = pick_residues(g);
+  if (ctx->R == 0) { delete ctx; return fail(MMP_E_INVAL, "y-z plane of %d x %d too large for pass B", ny, nz); }
   bool ok = make_plan(g.Px, ctx->plan_x) && make_plan(g.Py / ctx->R, ctx->plan_ly);
   if (!ok) { delete ctx; return fail(MMP_E_INVAL, "unsupported FFT length"); }
   launch_threads(g, ctx->R, &ctx->thrA, &ctx->thrB, &ctx->thrC);
@@ -614,17 +618,16 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
     cudaGetLastError();
     rc = fail(MMP_E_OOM, "pinned allocation failed");
   }
-  auto up = [&](float2*& dst, int P) {
+  auto up = [&](float2*& dst, const std::vector<float2>& w) {
     if (rc != MMP_OK) return;
-    std::vector<float2> w = roots(P);
-    rc = alloc_into(ctx, dst, P * sizeof(float2));
+    rc = alloc_into(ctx, dst, w.size() * sizeof(float2));
     if (rc == MMP_OK)
-      rc = cuda_check(ctx, cudaMemcpy(dst, w.data(), P * sizeof(float2), cudaMemcpyHostToDevice), "twiddles");
+      rc = cuda_check(ctx, cudaMemcpy(dst, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice), "twiddles");
   };
-  up(ctx->d_tw_x, g.Px);
-  up(ctx->d_tw_y, g.Py);
-  up(ctx->d_tw_ly, g.Py / ctx->R);
-  up(ctx->d_tw_z, g.Pz);
+  up(ctx->d_tw_x, pass_twiddles(ctx->plan_x));
+  up(ctx->d_tw_y, roots(g.Py));
+  up(ctx->d_tw_ly, pass_twiddles(ctx->plan_ly));
+  up(ctx->d_tw_z, roots(g.Pz));
 #undef CR
   if (rc == MMP_OK) rc = ensure_state(ctx);
   if (rc != MMP_OK) {

@@ -67,7 +67,7 @@ Layout plan_layout(const Grid& g, int R) {
   const long long ext = std::max<long long>({(long long)g.nx * g.ny * g.nz, (long long)g.kxn * g.ny * g.nz,
                                              (long long)g.kxn * g.kyn * g.nz, nk});
   L.T = take((size_t)g.kxn * 3 * g.nz * g.ny * sizeof(float2));
-  L.khat = take((size_t)nk * 6 * sizeof(float));
+  L.khat = take((size_t)g.kxn * g.kyn * g.krow * sizeof(float));
   L.buf0 = take((size_t)ext * 6 * sizeof(double));
   L.buf1 = take((size_t)ext * 6 * sizeof(double));
   const int P[3] = {g.Px, g.Py, g.Pz};
@@ -98,6 +98,8 @@ int set_up(Setup& S, int nx, int ny, int nz, const double* cell, cudaStream_t s)
   g.n = (long long)nx * ny * nz;
   g.Px = nice_length(nx); g.Py = nice_length(ny); g.Pz = nice_length(nz);
   g.kxn = g.Px / 2 + 1; g.kyn = g.Py / 2 + 1; g.kzn = g.Pz / 2 + 1;
+  g.krow = (6 * g.kzn + 3) & ~3;
+  g.ty = pick_tile_rows(g.ny, g.nz);
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (float)cell[a];
     g.ih[a] = (float)(1.0 / cell[a]);
@@ -105,6 +107,7 @@ int set_up(Setup& S, int nx, int ny, int nz, const double* cell, cudaStream_t s)
   if (g.Px > 4096 || g.Py > 4096 || g.Pz > 32)
     return err(MMP_E_INVAL, "demag: padded lengths must be <= 4096 (x, y) and nz <= 16");
   const int R = pick_residues(g);
+  if (R == 0) return err(MMP_E_INVAL, "y-z plane too large for pass B");
   DemagArgs d;
   memset(&d, 0, sizeof d);
   if (!make_plan(g.Px, d.plan_x) || !make_plan(g.Py / R, d.plan_ly)) return err(MMP_E_INVAL, "unsupported FFT length");
@@ -120,7 +123,8 @@ int set_up(Setup& S, int nx, int ny, int nz, const double* cell, cudaStream_t s)
     return cudaMemcpyAsync(b + off, src, bytes, cudaMemcpyHostToDevice, s);
   };
   cudaError_t e = cudaSuccess;
-  std::vector<float2> wx = roots(g.Px), wy = roots(g.Py), wly = roots(g.Py / R), wz = roots(g.Pz);
+  std::vector<float2> wx = pass_twiddles(d.plan_x), wy = roots(g.Py), wly = pass_twiddles(d.plan_ly),
+                     wz = roots(g.Pz);
   if (e == cudaSuccess) e = put(L.tw_x, wx.data(), wx.size() * sizeof(float2));
   if (e == cudaSuccess) e = put(L.tw_y, wy.data(), wy.size() * sizeof(float2));
   if (e == cudaSuccess) e = put(L.tw_ly, wly.data(), wly.size() * sizeof(float2));
@@ -153,6 +157,7 @@ int set_up(Setup& S, int nx, int ny, int nz, const double* cell, cudaStream_t s)
   kb.buf0 = reinterpret_cast<double*>(b + L.buf0);
   kb.buf1 = reinterpret_cast<double*>(b + L.buf1);
   kb.out = reinterpret_cast<float*>(b + L.khat);
+  kb.krow = g.krow;
   e = build_kernel_spectrum(kb, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_err(e, "mmp_demag_noalloc kernel build");

@@ -186,14 +186,18 @@ __global__ void k_tensor_axis(const double* __restrict__ in, double* __restrict_
   out[comp * per + r] = acc;
 }
 
-// Final scaling and layout change to float [kx][ky][kz][6].
+// Final scaling and layout change to float [kx][ky][krow], row = 6 floats
+// per kz (xx, yy, zz, xy, xz, yz) and zero padding to krow.
 __global__ void k_tensor_store(const double* __restrict__ in, float* __restrict__ out, int mx, int my,
-                               int mz, double scale_even, double scale_odd2) {
+                               int mz, int krow, double scale_even, double scale_odd2) {
   long long per = (long long)mx * my * mz;
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= per) return;
   int ix = idx % mx, iy = (idx / mx) % my, iz = idx / ((long long)mx * my);
-  long long o = (((long long)ix * my + iy) * mz + iz) * 6;
+  long long row = ((long long)ix * my + iy) * krow;
+  if (iz == 0)
+    for (int c = 6 * mz; c < krow; ++c) out[row + c] = 0.0f;
+  long long o = row + iz * 6;
   for (int c = 0; c < 6; ++c) out[o + c] = (float)(in[c * per + idx] * (c < 3 ? scale_even : scale_odd2));
 }
 
@@ -221,7 +225,8 @@ cudaError_t build_kernel_spectrum(const KernelBuild& kb, cudaStream_t s) {
   }
   double scale = -kMu0 / ((double)kb.P[0] * kb.P[1] * kb.P[2]);
   long long per = (long long)e[0] * e[1] * e[2];
-  k_tensor_store<<<(unsigned)((per + 127) / 128), 128, 0, s>>>(src, kb.out, e[0], e[1], e[2], scale, -scale);
+  k_tensor_store<<<(unsigned)((per + 127) / 128), 128, 0, s>>>(src, kb.out, e[0], e[1], e[2], kb.krow, scale,
+                                                                -scale);
   return cudaGetLastError();
 }
 
