@@ -230,7 +230,227 @@ WORKLOADS = {
           "demag+exchange+Zeeman; fixed DP45 dt 1e-13",
     "c3": "two-sublattice antiferromagnet 1024x256x1 cells of 2 nm with magnetoelastic coupling and "
           "elastodynamics (biaxial anisotropy, A0 -4e-11, A12 -1e-12); fixed DP45 dt 5e-15",
+    "c5": "served stream of relax-to-equilibrium solves: seeded Poisson arrivals (200 req/s), grids 64^2x1 "
+          "to 1024^2x4 of 4x4x2 nm, Ms 8e5, A 1.3e-11, alpha 0.5, |B| <= 50 mT, random m0; adaptive DP45 "
+          "(tol 1e-5) until max|m x B| <= torque tol or max time; 150 GB admission budget",
+    "c4": "256 independent ferromagnets, seeded nx, ny in {32..512} (2^k, 3*2^k), nz in {1,2,4}, 2 nm cells, "
+          "Ms 4e5-1.4e6, A 5e-12-2e-11, alpha 0.01-0.5, demag+exchange, random m0, fixed DP45 step per "
+          "instance (stability bound); batched: one launch per pass per stage, graph per lock step",
 }
+
+
+def run_serve(args):
+    """C5: continuous-batching relax server against the plain path (each
+    request relaxed alone, in arrival order) on the same request stream."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from inputs import serve_requests
+    from paper_2411_18194_gb300 import serve
+
+    def stream_of_requests():
+        return [serve.Request(i, w, t, args.torque_tol, args.max_time)
+                for i, (t, w) in enumerate(serve_requests(args.requests, rate_hz=args.rate))]
+
+    # warm-up: every distinct geometry once (spectrum builds, tuned shapes,
+    # module loading) so that both paths start warm
+    seen = set()
+    for r in stream_of_requests():
+        key = (tuple(r.workload.problem.shape), tuple(r.workload.problem.cell))
+        if key not in seen:
+            seen.add(key)
+            mag = serve._make_magnet(r.workload, 1e-14)
+            mag.step(1)
+            mag.close()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    srv = serve.RelaxServer(budget_bytes=args.budget_gb * 1e9, attempts_per_round=args.attempts)
+    served = srv.run(stream_of_requests())
+    peak = srv.peak_members
+    srv.close()
+    clk = clocks.stop()
+    st = serve.latency_stats(served)
+    plain = serve.latency_stats(serve.serve_one_at_a_time(stream_of_requests()))
+    (span,), (solves,) = reduce_over_ranks([st["span_s"]], [st["solves"]], "cuda")
+    if rank == 0:
+        line = {
+            "metric": "served solves/s", "baseline_metric": BASELINE_METRIC, "value": solves / span,
+            "unit": "solves/s", "n_gpus": ws, "steps": args.requests, "warmup": args.warmup,
+            "ms_per_step": span / max(1, st["solves"]) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded arrivals, grids, fields, m0)",
+            "config": {"workload": WORKLOADS["c5"], "requests": args.requests, "rate_hz": args.rate,
+                       "torque_tol_T": args.torque_tol, "max_time_s": args.max_time,
+                       "budget_gb": args.budget_gb, "attempts_per_round": args.attempts,
+                       "peak_members": peak, "parallelism": "replicas",
+                       "step": "one request (relax solve)"},
+            "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"]},
+            "plain_path": {"solves_per_s": plain["solves_per_s"], "p50": plain["p50_s"], "p99": plain["p99_s"],
+                           "mean": plain["mean_s"], "what": "each request relaxed alone (mmp_relax) in arrival order"},
+            "speedup_vs_plain": (solves / span) / plain["solves_per_s"],
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_batch(args):
+    """C4: the batch path against the plain one-at-a-time path on the same
+    instances (same shapes, same steps; results are bitwise equal)."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2411_18194_gb300 as pkg
+    from inputs import batch_instances
+    insts = batch_instances(args.instances)
+    mags = []
+    t0 = time.perf_counter()
+    for w in insts:
+        mag = pkg.Magnet.from_problem(w.problem)
+        mag.set_m(0, torch.from_numpy(w.m0[0]).cuda())
+        mag.set_solver(adaptive=False, dt=w.dt)
+        mags.append(mag)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    shapes = {}
+    for mag in mags:
+        sh, _ = mag.autotune(batch=True)
+        shapes[mag.shape] = sh
+    t_tune = time.perf_counter() - t0
+    cells = [int(np.prod(w.problem.shape)) for w in insts]
+    evals_per_step = 6 * sum(cells)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # batched path
+    b = pkg.Batch(stream)
+    for mag in mags:
+        b.add(mag, "steps", args.warmup + args.steps)
+    b.advance(args.warmup)          # first stages, graph capture, warm-up steps
+    clocks = ClockSampler(local)
+    barrier()
+    l0 = b.launches()
+    clocks.start()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    b.advance(args.steps)
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(stop)
+    launches = b.launches() - l0
+    b.close()
+    # per-pass device times (traced lock steps, direct launches) for the roofline
+    b = pkg.Batch(stream)
+    for mag in mags:
+        b.add(mag, "steps", 3)
+    b.advance(1)
+    b.profile(True)
+    b.advance(2)
+    prof = b.profile_read()
+    b.profile(False)
+    b.close()
+    # plain path: the same instances one at a time, same step count
+    for mag in mags:
+        mag.step(1)
+    barrier()
+    p0 = time.perf_counter()
+    for mag in mags:
+        mag.step(args.steps)
+    barrier()
+    ms_plain = (time.perf_counter() - p0) * 1e3
+    # end to end with host buffers: per lock step every state in from pinned
+    # host memory, one batched step, every state back
+    hosts = [torch.from_numpy(w.m0[0]).pin_memory() for w in insts]
+    outs = [torch.empty_like(h).pin_memory() for h in hosts]
+    e2e_steps = max(3, args.steps // 10)
+    b = pkg.Batch(stream)
+    for mag in mags:
+        b.add(mag, "steps", e2e_steps + 1)
+    b.advance(1)
+    barrier()
+    q0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for mag, h in zip(mags, hosts):
+            mag.set_m(0, h)
+        b.advance(1)
+        for mag, o in zip(mags, outs):
+            mag.get_m(0, o)
+    barrier()
+    e2e_s = time.perf_counter() - q0
+    b.close()
+    for mag in mags:
+        mag.close()
+    (t_max, t_plain), (all_evals,) = reduce_over_ranks([ms, ms_plain], [evals_per_step * args.steps], "cuda")
+    value = all_evals / (t_max * 1e-3) / 1e6
+    plain = all_evals / (t_plain * 1e-3) / 1e6
+    e2e_value = evals_per_step * e2e_steps / e2e_s / 1e6
+    _, (e2e_all,) = reduce_over_ranks([], [e2e_value], "cuda")
+    peak, src = peaks()
+    step_bytes = 0
+    pass_bytes = {"pass_a": 0, "pass_b": 0, "field": 0}
+    nk_avg = (0 + 1 + 2 + 3 + 4 + 5 + 5) / 7.0
+    for w in insts:
+        kb = kernel_bytes(geometry(w.problem.shape), nk_avg)
+        step_bytes += 6 * sum(kb.values())
+        for k in pass_bytes:
+            pass_bytes[k] += kb[k]
+    # dominant pass: all its launches of one stage (pass B: one per z group)
+    dom = max(prof, key=lambda k: prof[k][1])
+    per_stage = {k: v[1] / 12.0 for k, v in prof.items()}    # 2 traced lock steps x 6 stages
+    achieved = pass_bytes[dom] / (per_stage[dom] * 1e-3) / 1e9
+    share = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
+    nbytes = 12 * sum(cells)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "baseline_metric": BASELINE_METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded sizes, materials, random m0)",
+            "config": {"workload": WORKLOADS["c4"], "instances": len(insts), "cells": sum(cells),
+                       "parallelism": "replicas",
+                       "step": "one lock step: one fixed DP45 step of every instance (6 evaluations each)",
+                       "l2": "inputs larger than L2 (%.1f GB of state, stages, spectra)" % (
+                           sum(cells) * 150e-9),
+                       "setup_s": round(t_setup, 2), "autotune_s": round(t_tune, 2),
+                       "distinct_shapes": len(shapes)},
+            "plain_path": {"value": plain, "unit": UNIT, "ms_per_step": t_plain / args.steps,
+                           "what": "the same instances stepped one at a time through mmp_step"},
+            "speedup_vs_plain": value / plain,
+            "solves_per_s": {"batched": len(insts) * ws / (t_max * 1e-3),
+                             "plain": len(insts) * ws / (t_plain * 1e-3),
+                             "solve": "%d fixed DP45 steps of one instance" % args.steps},
+            "roofline": {"kernel": "batched " + dom + " (all its launches of one stage)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "peak_source": src, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "bytes_per_stage": pass_bytes[dom],
+                         "ms_per_stage": per_stage[dom]},
+            "kernel_share": share,
+            "whole_step_gbs": step_bytes * args.steps / (ms * 1e-3) / 1e9,
+            "cpu_baseline": None,
+            "e2e": {"value": e2e_all, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_gpu(args):
@@ -381,14 +601,26 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-evals", type=int, default=0)
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"],
-                    help="c2 (default, the benchmark line); c1, c3 for the other workloads")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default, the benchmark line); c1, c3 for the other single workloads; "
+                         "c4 the batch of uneven instances; c5 the served request stream")
+    ap.add_argument("--instances", type=int, default=256, help="c4: number of instances")
+    ap.add_argument("--requests", type=int, default=48, help="c5: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="c5: mean arrival rate (1/s)")
+    ap.add_argument("--torque-tol", type=float, default=1e-2, help="c5: relax torque tolerance (T)")
+    ap.add_argument("--max-time", type=float, default=20e-12, help="c5: relax max simulated time (s)")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="c5: admission budget (GB)")
+    ap.add_argument("--attempts", type=int, default=4, help="c5: lock-step attempts between admissions")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.profile_evals:
         run_profile_evals(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_batch(args)
+    elif args.workload == "c5":
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -29,6 +29,12 @@
  *     return MMP_E_STATE.  Unsupported requests fail with MMP_E_INVAL; the
  *     library never falls back to another code path.
  *   - One context must be used by one host thread at a time.
+ *   - The demag kernel spectrum (the FFT of -mu0 N, FP32, about 4 * 6 *
+ *     (nz + 1) / nz bytes per cell) is built on the first evaluation and
+ *     shared by every context of the process with the same extents and
+ *     cell size on the same device: it is library-owned cudaMalloc memory
+ *     (not taken through the context allocator), freed with the last such
+ *     context.
  */
 #ifndef MMP_H
 #define MMP_H
@@ -217,6 +223,95 @@ int mmp_profile_read(mmp_ctx* ctx, int kernel, long long* launches, double* tota
 #define MMP_NOALLOC_SCRATCH_BYTES (32 * 1024 * 1024)
 int mmp_demag_noalloc(int nx, int ny, int nz, double cx, double cy, double cz, const float* M, float* B,
                       void* stream);
+
+/* ---------------------------------------------------------------------
+ * Launch shape and autotuning (no counterpart in the paper: how the FFT
+ * passes of Methods, Magnetostatic field are laid out on the GPU).
+ * --------------------------------------------------------------------- */
+typedef struct mmp_shape {
+    int ty;            /* rows (y) per tile of the x-FFT passes: 2, 4 or 8 */
+    int radix_x;       /* x FFT plan: 0 = radix-16 passes first, 1 = radix-8 passes */
+    int radix_y;       /* plan of the y FFT of pass B (length Py/R), same choices */
+    int R;             /* ky residue classes = CTAs per pass-B cluster: 1, 2, 4 or 8 */
+    int stage_kernel;  /* 1: pass B stages its slice of the kernel octant in shared memory */
+} mmp_shape;
+
+/* Current shape of the context (chosen at creation: ty from the grid, the
+ * radix-16 plans, the smallest R that fits, stage_kernel = 1). */
+int mmp_get_shape(mmp_ctx* ctx, mmp_shape* out);
+
+/* Set a shape.  MMP_E_INVAL (context unchanged) if it does not fit the grid
+ * (shared memory above 227 KB, FFT capacity, R not dividing Py).  The plans
+ * change the FP32 rounding order of the transforms, so the cached first
+ * Runge-Kutta stage is dropped; results agree to FP32 rounding. */
+int mmp_set_shape(mmp_ctx* ctx, const mmp_shape* shape);
+
+#define MMP_TUNE_BATCH 1   /* only shapes a batch runs (R = 1, stage_kernel = 0) */
+#define MMP_TUNE_FORCE 2   /* time again even if this geometry was tuned before */
+/* Time every valid shape on the context's current state (a few evaluations
+ * of passes A, B and C each, CUDA events on the context's stream), set the
+ * fastest and return it (chosen, may be NULL) with its time per field
+ * evaluation in ms (eval_ms, may be NULL).  Results are cached per
+ * (grid, sublattices, flags) in the process; a cached geometry is set
+ * without timing unless MMP_TUNE_FORCE.  Synchronises the stream. */
+int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms);
+
+/* ---------------------------------------------------------------------
+ * Batches: independent contexts advanced together (no counterpart in the
+ * paper, which runs one simulation at a time).  Every Dormand-Prince stage
+ * of all active members is one persistent kernel launch over a work list of
+ * (member, tile) items; lock steps of fixed-step members are replayed from
+ * a CUDA graph.  A member runs exactly the arithmetic of its own context
+ * (same plans and coefficients), so its results are bitwise those of
+ * mmp_step / mmp_run / mmp_relax on the same context with the same shape.
+ *
+ * Members: one sublattice, one region (no region map), the demag term on,
+ * no AFM / magnetoelastic / elastic terms, shape R = 1 and stage_kernel = 0
+ * (mmp_set_shape or mmp_autotune with MMP_TUNE_BATCH first); otherwise
+ * MMP_E_INVAL.  The batch borrows its members: while a context is a member
+ * it must not be used elsewhere, and it must be removed before it is
+ * destroyed.  Between mmp_batch_advance calls every member's state sits in
+ * its context as usual (mmp_get_m, mmp_get_time work).  All work runs on
+ * the batch's stream; the calls synchronise it before returning.
+ * --------------------------------------------------------------------- */
+typedef struct mmp_batch mmp_batch;
+
+enum mmp_goal {
+    MMP_GOAL_STEPS = 0,  /* a = number of accepted steps (fixed or adaptive per the member's solver) */
+    MMP_GOAL_RUN = 1,    /* a = duration (s); the last step lands on time */
+    MMP_GOAL_RELAX = 2   /* a = torque tolerance (T), c = max simulated time (s); as mmp_relax */
+};
+
+/* `stream`: the cudaStream_t all batch work runs on; NULL (the legacy
+ * default stream, on which graphs cannot be captured) makes the batch
+ * create and own a non-blocking stream. */
+int mmp_batch_create(mmp_batch** out, void* stream);
+/* Destroys the batch, not its members. */
+int mmp_batch_destroy(mmp_batch* b);
+/* Add a member with its goal (counted from its current time / steps). */
+int mmp_batch_add(mmp_batch* b, mmp_ctx* ctx, int goal, double a, double c);
+int mmp_batch_remove(mmp_batch* b, mmp_ctx* ctx);
+int mmp_batch_size(mmp_batch* b, int* n);
+/* Run up to max_attempts lock-step attempts; a member stops taking part
+ * once its goal is reached.  Adaptive or relaxing members read their
+ * error estimates back once per lock step (one synchronisation for the
+ * whole batch).  n_active (may be NULL) receives the members not done.
+ * MMP_E_TIMEOUT if a dependency wait inside the stage kernel ran past its
+ * limit (the step is then invalid and should be discarded). */
+int mmp_batch_advance(mmp_batch* b, int max_attempts, int* n_active);
+/* done: goal reached (or failed); status: MMP_OK or the member's error
+ * (MMP_E_NONFINITE: its state is the last accepted one). */
+int mmp_batch_status(mmp_batch* b, mmp_ctx* ctx, int* done, int* status);
+/* Kernel launches the batch has made (tracing). */
+int mmp_batch_launches(mmp_batch* b, long long* n);
+/* Tracing: with enable != 0 (counters reset) every pass launch is bracketed
+ * by CUDA events and fixed-step lock steps launch directly instead of
+ * through the graph; mmp_batch_profile_read returns, for pass 0 (A: stage
+ * assembly + forward x FFT), 1 (B: y/z transforms + kernel multiply, all z
+ * groups) or 2 (C: inverse x FFT + field + torque), the launches and their
+ * summed device time since the reset.  Both synchronise the batch stream. */
+int mmp_batch_profile(mmp_batch* b, int enable);
+int mmp_batch_profile_read(mmp_batch* b, int pass, long long* launches, double* total_ms);
 
 /* Wait for all work of the context. */
 int mmp_sync(mmp_ctx* ctx);

@@ -8,11 +8,11 @@ CPU oracle and the CUDA path receive the same FP32-rounded arrays from here.
 from .rng import splitmix64, uniform01, random_unit_vectors, noisy_axis_vectors
 from .problem import (Problem, GAMMA, MU0, PARAM_SCALARS, PARAM_VECTORS,
                       TERMS, config_c1, config_c2, config_c3, config_small,
-                      batch_instances, serve_requests)
+                      batch_instances, serve_requests, stable_dt)
 
 __all__ = [
     "splitmix64", "uniform01", "random_unit_vectors", "noisy_axis_vectors",
     "Problem", "GAMMA", "MU0", "PARAM_SCALARS", "PARAM_VECTORS", "TERMS",
     "config_c1", "config_c2", "config_c3", "config_small", "batch_instances",
-    "serve_requests",
+    "serve_requests", "stable_dt",
 ]

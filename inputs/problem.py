@@ -191,9 +191,22 @@ def config_small(shape, cell, seed, terms=("DEMAG", "EXCH", "ANIS", "DMI", "ZEEM
 BATCH_SIZES = (32, 64, 96, 128, 192, 256, 384, 512)
 
 
+def stable_dt(p, courant=0.25):
+    """A fixed DP45 step for an explicit run of problem p: `courant` over the
+    fastest precession rate gamma * B_max, with B_max the largest exchange
+    field of a discrete Laplacian (2A/Ms * 4/h^2 per axis with more than one
+    cell) plus mu0 Ms.  A workload parameter, not part of the method."""
+    ms = float(p.scal["MS"][0].max())
+    a = float(p.scal["AEX"][0].max())
+    lap = sum(4.0 / h ** 2 for h, n in zip(p.cell, p.shape) if n > 1)
+    bmax = 2.0 * a / ms * lap + MU0 * ms
+    return courant / (GAMMA * bmax)
+
+
 def batch_instances(count=256, seed=BASE_SEED + 3):
     """Independent ferromagnets with seeded uneven sizes and materials
-    (demag + exchange, 2 nm cubes, random initial state)."""
+    (demag + exchange, 2 nm cubes, random initial state), each with its own
+    fixed step (stable_dt)."""
     out = []
     r = uniform01(seed, np.arange(8 * count, dtype=np.uint64)).reshape(count, 8)
     for i in range(count):
@@ -204,7 +217,7 @@ def batch_instances(count=256, seed=BASE_SEED + 3):
         p.set("MS", 4e5 + 1e6 * r[i, 3]).set("AEX", 5e-12 + 1.5e-11 * r[i, 4])
         p.set("ALPHA", 0.01 + 0.49 * r[i, 5])
         s = seed * 1000 + i
-        out.append(Workload("instance %d" % i, p, [random_unit_vectors(s, p.shape)], seed=s))
+        out.append(Workload("instance %d" % i, p, [random_unit_vectors(s, p.shape)], seed=s, dt=stable_dt(p)))
     return out
 
 

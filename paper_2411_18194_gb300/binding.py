@@ -22,6 +22,19 @@ GLOBAL_IDS = {"A0": 0, "A12": 1, "LATTICE_A": 2, "C11": 3, "C12": 4, "C44": 5, "
 STATUS = {0: "MMP_OK", -1: "MMP_E_INVAL", -2: "MMP_E_OOM", -3: "MMP_E_CUDA", -4: "MMP_E_NONFINITE",
           -5: "MMP_E_TIMEOUT", -6: "MMP_E_STATE"}
 
+GOALS = {"steps": 0, "run": 1, "relax": 2}
+TUNE_BATCH, TUNE_FORCE = 1, 2
+
+
+class Shape(ctypes.Structure):
+    """mmp_shape: launch shape of the demag passes."""
+    _fields_ = [("ty", ctypes.c_int), ("radix_x", ctypes.c_int), ("radix_y", ctypes.c_int),
+                ("R", ctypes.c_int), ("stage_kernel", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -59,6 +72,20 @@ _SIGS = {
                            _c.c_void_p, _c.c_void_p], _c.c_int),
     "mmp_profile_read": ([_c.c_void_p, _c.c_int, _c.POINTER(_c.c_longlong), _c.POINTER(_c.c_double)],
                          _c.c_int),
+    "mmp_get_shape": ([_c.c_void_p, _c.POINTER(Shape)], _c.c_int),
+    "mmp_set_shape": ([_c.c_void_p, _c.POINTER(Shape)], _c.c_int),
+    "mmp_autotune": ([_c.c_void_p, _c.c_int, _c.POINTER(Shape), _c.POINTER(_c.c_double)], _c.c_int),
+    "mmp_batch_create": ([_c.POINTER(_c.c_void_p), _c.c_void_p], _c.c_int),
+    "mmp_batch_destroy": ([_c.c_void_p], _c.c_int),
+    "mmp_batch_add": ([_c.c_void_p, _c.c_void_p, _c.c_int, _c.c_double, _c.c_double], _c.c_int),
+    "mmp_batch_remove": ([_c.c_void_p, _c.c_void_p], _c.c_int),
+    "mmp_batch_size": ([_c.c_void_p, _c.POINTER(_c.c_int)], _c.c_int),
+    "mmp_batch_advance": ([_c.c_void_p, _c.c_int, _c.POINTER(_c.c_int)], _c.c_int),
+    "mmp_batch_status": ([_c.c_void_p, _c.c_void_p, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)], _c.c_int),
+    "mmp_batch_launches": ([_c.c_void_p, _c.POINTER(_c.c_longlong)], _c.c_int),
+    "mmp_batch_profile": ([_c.c_void_p, _c.c_int], _c.c_int),
+    "mmp_batch_profile_read": ([_c.c_void_p, _c.c_int, _c.POINTER(_c.c_longlong), _c.POINTER(_c.c_double)],
+                               _c.c_int),
 }
 KERNEL_IDS = {"pass_a": 0, "pass_b": 1, "field": 2, "assemble": 3, "strain": 4, "elastic": 5}
 
@@ -277,6 +304,27 @@ class Magnet:
                 out[name] = (n.value, ms.value)
         return out
 
+    # -------------------------------------------------------------- shape --
+    def get_shape(self):
+        sh = Shape()
+        _check(library().mmp_get_shape(self._ctx, ctypes.byref(sh)))
+        return sh.as_dict()
+
+    def set_shape(self, **kw):
+        """Change fields of the launch shape (ty, radix_x, radix_y, R, stage_kernel)."""
+        d = self.get_shape()
+        d.update(kw)
+        sh = Shape(**d)
+        _check(library().mmp_set_shape(self._ctx, ctypes.byref(sh)))
+        return d
+
+    def autotune(self, batch=False, force=False):
+        """Time the valid shapes, keep the fastest; returns (shape, ms per evaluation)."""
+        sh, ms = Shape(), ctypes.c_double()
+        flags = (TUNE_BATCH if batch else 0) | (TUNE_FORCE if force else 0)
+        _check(library().mmp_autotune(self._ctx, flags, ctypes.byref(sh), ctypes.byref(ms)))
+        return sh.as_dict(), ms.value
+
     # ------------------------------------------------------------ helpers --
     @classmethod
     def from_problem(cls, problem, **kw):
@@ -309,3 +357,85 @@ class Magnet:
             mag.set_global(name, problem.glob.get(name, 0.0))
         mag.enable_terms(sorted(problem.terms))
         return mag
+
+
+class Batch:
+    """A set of Magnets advanced together (an mmp_batch).
+
+    Members keep their own state; between advance() calls each Magnet can be
+    read as usual.  Goals: ("steps", n), ("run", duration), ("relax",
+    torque_tol, max_time)."""
+
+    def __init__(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        b = ctypes.c_void_p()
+        _check(library().mmp_batch_create(ctypes.byref(b), ctypes.c_void_p(handle)))
+        self._b = b
+        self._members = {}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            library().mmp_batch_destroy(self._b)
+            self._b = None
+            self._members = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add(self, mag, goal="steps", a=0.0, c=0.0):
+        _check(library().mmp_batch_add(self._b, mag._ctx, GOALS[goal], float(a), float(c)))
+        self._members[id(mag)] = mag
+
+    def remove(self, mag):
+        _check(library().mmp_batch_remove(self._b, mag._ctx))
+        self._members.pop(id(mag), None)
+
+    def __len__(self):
+        n = ctypes.c_int()
+        _check(library().mmp_batch_size(self._b, ctypes.byref(n)))
+        return n.value
+
+    def advance(self, max_attempts=1 << 30):
+        """Lock-step attempts until every member's goal is met (or max_attempts);
+        returns the number of members not done."""
+        n = ctypes.c_int()
+        _check(library().mmp_batch_advance(self._b, int(max_attempts), ctypes.byref(n)))
+        return n.value
+
+    def status(self, mag):
+        """(done, status) of a member."""
+        d, st = ctypes.c_int(), ctypes.c_int()
+        _check(library().mmp_batch_status(self._b, mag._ctx, ctypes.byref(d), ctypes.byref(st)))
+        return bool(d.value), st.value
+
+    def launches(self):
+        n = ctypes.c_longlong()
+        _check(library().mmp_batch_launches(self._b, ctypes.byref(n)))
+        return n.value
+
+    def profile(self, enable=True):
+        """Start (reset) or stop per-pass CUDA-event timing."""
+        _check(library().mmp_batch_profile(self._b, int(bool(enable))))
+
+    def profile_read(self):
+        """{pass: (launches, total device ms)} since the last reset."""
+        out = {}
+        for name, k in (("pass_a", 0), ("pass_b", 1), ("field", 2)):
+            n, ms = ctypes.c_longlong(), ctypes.c_double()
+            _check(library().mmp_batch_profile_read(self._b, k, ctypes.byref(n), ctypes.byref(ms)))
+            if n.value:
+                out[name] = (n.value, ms.value)
+        return out

@@ -12,20 +12,23 @@
 
 namespace mmp {
 
-// L = 16^n16 * (8, 4 or 2 once) * 3^n3, applied in that order.  (A runtime
-// list of radices dispatched in one loop made the compiler keep the pass
-// registers in local memory; fixed branches do not.)
+// L = 16^n16 * 8^n8 * (4 or 2 once) * 3^n3, applied in that order.  (A
+// runtime list of radices dispatched in one loop made the compiler keep the
+// pass registers in local memory; fixed branches do not.)
 struct FftPlan {
   int L;
   int n16, n8, n4, n2, n3;
+  int lin;   // every pass takes the uniform-stride addressing (stockham_pass)
 };
 
 // Shared-memory layout of a batch of transforms: element i of transform t
-// sits at t * fft_pitch(L) + i + i/32.  One padding slot per 32 elements
-// turns the stride-R stores of the early Stockham passes into distinct
-// banks; the odd pitch staggers the starts of successive transforms.
-__host__ __device__ __forceinline__ int fft_pitch(int L) { return L + (L >> 5) + 1; }
-__device__ __forceinline__ int fidx(int t, int i, int pitch) { return t * pitch + i + (i >> 5); }
+// sits at t * fft_pitch(L) + pad(i), pad(i) = i + i/16.  One padding slot
+// per 16 complex values (128 bytes, one pass over the 32 banks) turns the
+// stride-16 stores of a first radix-16 pass into stride 17, conflict-free;
+// the odd pitch staggers the starts of successive transforms.
+__host__ __device__ __forceinline__ int fft_pitch(int L) { return L + (L >> 4) + 1; }
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+__device__ __forceinline__ int fidx(int t, int i, int pitch) { return t * pitch + fpad(i); }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -147,13 +150,24 @@ struct PassCap { static constexpr int B = (R == 3) ? CAP / 3 : CAP / R; };
 // Twiddles of this pass: tw[(r-1) Ns + k] = w_{Ns R}^{r k} (pass-ordered
 // table, see pass_twiddles() on the host), so lanes with consecutive k read
 // consecutive words.
+//
+// Addressing: pad(a + b) = pad(a) + pad(b) whenever (a mod 16) + (b mod 16)
+// < 16.  So the loads j + r L/R (j < L/R) of a pass sit at
+// pad(j) + r * ls, ls = pad(L/R), when L/R is a multiple of 16 (or the whole
+// transform is shorter than 16), and the stores o + r Ns (o = (j - k) R + k,
+// k < Ns) at pad(o) + r * ss when Ns is a multiple of 16 (ss = pad(Ns)) or a
+// power-of-two radix keeps R Ns <= 16 (ss = Ns).  Every pass of the
+// power-of-two lengths from 256 up is of that kind: one padded base per
+// butterfly and a uniform stride.  Other passes form each index.
 // Requires L*nbatch <= (CAP/R)*R*blockDim.x (checked by the host).
-template <int R, bool INV, int CAP>
+template <int R, bool INV, int CAP, bool LIN>
 __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, int Ns, const float2* tw) {
   constexpr int MAXB = PassCap<R, CAP>::B;
   const int nbf = L / R;
   const int total = nbf * nbatch;
   const int pitch = fft_pitch(L);
+  const int ls = (nbf & 15) == 0 ? fpad(nbf) : nbf;   // used when LIN
+  const int ss = (Ns & 15) == 0 ? fpad(Ns) : Ns;
   // t = b / nbf without an integer division: (b + 1/2) / nbf is at least
   // 1/(2 nbf) away from an integer and b, nbf < 2^15, so the FP32 quotient
   // truncates exactly.
@@ -164,8 +178,15 @@ __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, i
     int b = threadIdx.x + i * blockDim.x;
     if (b < total) {
       int t = (int)(((float)b + 0.5f) * rnbf), j = b - t * nbf;
+      const float2* src = data + t * pitch;
+      if (LIN) {
+        const float2* p = src + fpad(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = data[fidx(t, j + r * nbf, pitch)];
+        for (int r = 0; r < R; ++r, p += ls) v[i][r] = *p;
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[i][r] = src[fpad(j + r * nbf)];
+      }
     }
   }
   __syncthreads();
@@ -186,8 +207,15 @@ __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, i
       }
       dft<R, INV>(v[i]);
       const int o = (j - k) * R + k;
+      float2* dst = data + t * pitch;
+      if (LIN) {
+        float2* p = dst + fpad(o);
 #pragma unroll
-      for (int r = 0; r < R; ++r) data[fidx(t, o + r * Ns, pitch)] = v[i][r];
+        for (int r = 0; r < R; ++r, p += ss) *p = v[i][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[fpad(o + r * Ns)] = v[i][r];
+      }
     }
   }
   __syncthreads();
@@ -196,25 +224,38 @@ __device__ __forceinline__ void stockham_pass(float2* data, int L, int nbatch, i
 // Full transform of a batch in shared memory (natural order in and out).
 // Callers __syncthreads() before (data written) and may read right after.
 // `tw` is the pass-ordered twiddle table of the plan (L - 1 entries) in
-// shared or global memory.
-template <bool INV, int CAP = 32>
-__device__ __forceinline__ void block_fft(float2* data, const FftPlan p, int nbatch, const float2* tw) {
+// shared or global memory.  The addressing variant is chosen once per
+// transform (p.lin): mixing both in one pass loop made the compiler keep the
+// address offsets of both live and spill.
+template <bool INV, int CAP, bool LIN>
+__device__ __forceinline__ void block_fft_v(float2* data, const FftPlan p, int nbatch, const float2* tw) {
   int Ns = 1;
 #pragma unroll 1
   for (int s = 0; s < p.n16; ++s) {
-    stockham_pass<16, INV, CAP>(data, p.L, nbatch, Ns, tw);
+    stockham_pass<16, INV, CAP, LIN>(data, p.L, nbatch, Ns, tw);
     if (Ns > 1) tw += 15 * Ns;
     Ns *= 16;
   }
-  if (p.n8) { stockham_pass<8, INV, CAP>(data, p.L, nbatch, Ns, tw); if (Ns > 1) tw += 7 * Ns; Ns *= 8; }
-  if (p.n4) { stockham_pass<4, INV, CAP>(data, p.L, nbatch, Ns, tw); if (Ns > 1) tw += 3 * Ns; Ns *= 4; }
-  if (p.n2) { stockham_pass<2, INV, CAP>(data, p.L, nbatch, Ns, tw); if (Ns > 1) tw += Ns; Ns *= 2; }
+#pragma unroll 1
+  for (int s = 0; s < p.n8; ++s) {
+    stockham_pass<8, INV, CAP, LIN>(data, p.L, nbatch, Ns, tw);
+    if (Ns > 1) tw += 7 * Ns;
+    Ns *= 8;
+  }
+  if (p.n4) { stockham_pass<4, INV, CAP, LIN>(data, p.L, nbatch, Ns, tw); if (Ns > 1) tw += 3 * Ns; Ns *= 4; }
+  if (p.n2) { stockham_pass<2, INV, CAP, LIN>(data, p.L, nbatch, Ns, tw); if (Ns > 1) tw += Ns; Ns *= 2; }
 #pragma unroll 1
   for (int s = 0; s < p.n3; ++s) {
-    stockham_pass<3, INV, CAP>(data, p.L, nbatch, Ns, tw);
+    stockham_pass<3, INV, CAP, LIN>(data, p.L, nbatch, Ns, tw);
     if (Ns > 1) tw += 2 * Ns;
     Ns *= 3;
   }
+}
+
+template <bool INV, int CAP = 32>
+__device__ __forceinline__ void block_fft(float2* data, const FftPlan p, int nbatch, const float2* tw) {
+  if (p.lin) block_fft_v<INV, CAP, true>(data, p, nbatch, tw);
+  else block_fft_v<INV, CAP, false>(data, p, nbatch, tw);
 }
 
 }  // namespace mmp

@@ -56,6 +56,7 @@ struct DemagArgs {
   const float2* tw_z;        // Pz roots
   FftPlan plan_x, plan_ly;
   int R;                     // residue classes of ky per cluster
+  int ks;                    // pass B stages the kernel slice in shared memory
 };
 
 struct Coefs {
@@ -105,23 +106,25 @@ struct PassBSmem {
   size_t twl, twf, twc, ks, total;
 };
 
-__host__ __device__ __forceinline__ PassBSmem passb_smem(int ny, int nz, int Py, int kzn, int R) {
+// The fold and recombination twiddles exist only for R > 1; the kernel
+// slice only when it is staged (ks).
+__host__ __device__ __forceinline__ PassBSmem passb_smem(int ny, int nz, int Py, int kzn, int R, bool ks) {
   const int Ly = Py / R;
   const int cnt = (ny + R - 1) / R;
   PassBSmem s;
   size_t at = (size_t)3 * nz * fft_pitch(Ly) * sizeof(float2);
   s.twl = at; at += (size_t)Ly * sizeof(float2);
-  s.twf = at; at += (size_t)Ly * sizeof(float2);
-  s.twc = at; at += (size_t)cnt * sizeof(float2);
+  s.twf = at; if (R > 1) at += (size_t)Ly * sizeof(float2);
+  s.twc = at; if (R > 1) at += (size_t)cnt * sizeof(float2);
   at = (at + 15) & ~(size_t)15;   // 16-byte rows for cp.async
-  s.ks = at; at += (size_t)Ly * ((6 * kzn + 3) & ~3) * sizeof(float);
+  s.ks = at; if (ks) at += (size_t)Ly * ((6 * kzn + 3) & ~3) * sizeof(float);
   s.total = at;
   return s;
 }
 
 // shared memory bytes of each pass (host side planning)
 size_t smem_passA(const Grid& g);
-size_t smem_passB(const Grid& g, int R);
+size_t smem_passB(const Grid& g, int R, bool ks);
 size_t smem_field(const Grid& g, bool demag);
 
 }  // namespace mmp

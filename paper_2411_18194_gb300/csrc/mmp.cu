@@ -8,10 +8,15 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
+#include "ctx.h"
+#include "dp45.h"
 #include "kernels.h"
 #include "mmp.h"
 #include "plan.h"
@@ -32,19 +37,6 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-// Dormand and Prince (1980) RK5(4)7FM tableau, FSAL, local extrapolation.
-const double kA[7][6] = {
-    {0, 0, 0, 0, 0, 0},
-    {1.0 / 5, 0, 0, 0, 0, 0},
-    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
-    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
-    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
-    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
-    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
-const double kB4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100,
-                       1.0 / 40};
-// step-size controller (a reading of what the paper leaves open)
-const double kSafety = 0.9, kGrowMin = 0.2, kGrowMax = 5.0, kExponent = 0.2;
 const double kRc = 10.0;   // Newell below 10 max(cell), asymptotic above
 
 float2 split(double v) {
@@ -53,55 +45,6 @@ float2 split(double v) {
 }
 
 }  // namespace
-
-struct mmp_ctx {
-  Grid g;
-  int nsub = 1;
-  double cell[3];
-  cudaStream_t stream = nullptr;
-  mmp_alloc_fn ualloc = nullptr;
-  mmp_free_fn ufree = nullptr;
-  void* uuser = nullptr;
-  bool poisoned = false;
-  unsigned terms = 0;
-  // parameter tables (FP64)
-  double scal[MMP_NPARAM][2][MMP_MAX_REGIONS];
-  double vec[MMP_NPARAM3][2][MMP_MAX_REGIONS][3];
-  double glob[MMP_NGLOBAL];
-  bool uniform = true;
-  bool used[MMP_MAX_REGIONS] = {true};   // regions present in the map
-  bool coef_dirty = true, khat_dirty = true;
-  // device buffers
-  uint8_t* d_regions = nullptr;
-  RegionCoef* d_coef = nullptr;
-  float2* d_hA = nullptr;
-  float* d_y = nullptr;
-  float* d_stage = nullptr;
-  float* d_k[7] = {};
-  float* d_B = nullptr;
-  float* d_eps = nullptr;
-  float* d_sig = nullptr;
-  float2* d_T = nullptr;
-  float* d_khat = nullptr;
-  float2 *d_tw_x = nullptr, *d_tw_y = nullptr, *d_tw_ly = nullptr, *d_tw_z = nullptr;
-  unsigned* d_red = nullptr;   // [0] error bits, [1] torque bits
-  unsigned* h_red = nullptr;   // pinned
-  int nparts = 0;              // 3-vectors in the state
-  long long nstate = 0;        // floats in the state
-  FftPlan plan_x{}, plan_ly{};
-  int R = 1, thrA = 256, thrB = 256, thrC = 256;
-  // solver
-  int adaptive = 0;
-  double dt = 1e-13, tol = 1e-5, dt_min = 1e-18, dt_max = 1e-11;
-  double t = 0.0;
-  long long steps = 0, rejected = 0, evals = 0;
-  bool k1_valid = false;
-  int k1_relax = 0;
-  // tracing
-  bool prof = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[MMP_NKERNEL];
-  size_t prof_used[MMP_NKERNEL] = {};
-};
 
 namespace {
 
@@ -253,11 +196,55 @@ int upload_coefs(mmp_ctx* ctx) {
   return MMP_OK;
 }
 
+// Resident demag kernel spectra, shared by every context of the process
+// with the same extents and cell size on the same device (reference
+// counted; library-owned cudaMalloc memory).
+struct KhatEntry {
+  float* ptr = nullptr;
+  int refs = 0;
+};
+using KhatKey = std::tuple<int, int, int, int, double, double, double>;
+std::mutex g_khat_mu;
+std::map<KhatKey, KhatEntry> g_khat;
+
+KhatKey khat_key(const mmp_ctx* ctx) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return KhatKey(dev, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->cell[0], ctx->cell[1], ctx->cell[2]);
+}
+
+void release_khat(mmp_ctx* ctx) {
+  if (!ctx->d_khat) return;
+  std::lock_guard<std::mutex> lk(g_khat_mu);
+  auto it = g_khat.find(ctx->khat_key);
+  if (it != g_khat.end() && it->second.ptr == ctx->d_khat && --it->second.refs == 0) {
+    cudaFree(it->second.ptr);
+    g_khat.erase(it);
+  }
+  ctx->d_khat = nullptr;
+}
+
 int build_khat(mmp_ctx* ctx) {
   if (!ctx->khat_dirty) return MMP_OK;
   const Grid& g = ctx->g;
+  const KhatKey key = khat_key(ctx);
+  std::lock_guard<std::mutex> lk(g_khat_mu);
+  {
+    auto it = g_khat.find(key);
+    if (it != g_khat.end()) {
+      it->second.refs++;
+      ctx->d_khat = it->second.ptr;
+      ctx->khat_key = key;
+      ctx->khat_dirty = false;
+      return MMP_OK;
+    }
+  }
   size_t nk = (size_t)g.kxn * g.kyn * g.kzn;
-  TRY(alloc_into(ctx, ctx->d_khat, (size_t)g.kxn * g.kyn * g.krow * sizeof(float)));
+  float* khat = nullptr;
+  if (cudaMalloc(&khat, (size_t)g.kxn * g.kyn * g.krow * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MMP_E_OOM, "allocation of the demag kernel spectrum failed");
+  }
   long long ext = std::max<long long>({(long long)g.nx * g.ny * g.nz, (long long)g.kxn * g.ny * g.nz,
                                        (long long)g.kxn * g.kyn * g.nz, (long long)nk});
   double* b0 = nullptr;
@@ -287,7 +274,7 @@ int build_khat(mmp_ctx* ctx) {
     kb.rc = kRc;
     kb.buf0 = b0;
     kb.buf1 = b1;
-    kb.out = ctx->d_khat;
+    kb.out = khat;
     kb.krow = g.krow;
     rc = cuda_check(ctx, build_kernel_spectrum(kb, ctx->stream), "demag kernel build");
     if (rc == MMP_OK) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "demag kernel build (sync)");
@@ -295,8 +282,18 @@ int build_khat(mmp_ctx* ctx) {
   dfree(ctx, b0);
   dfree(ctx, b1);
   for (int a = 0; a < 3; ++a) dfree(ctx, trig[a]);
-  if (rc == MMP_OK) ctx->khat_dirty = false;
-  return rc;
+  if (rc != MMP_OK) {
+    cudaFree(khat);
+    return rc;
+  }
+  KhatEntry e;
+  e.ptr = khat;
+  e.refs = 1;
+  g_khat[key] = e;
+  ctx->d_khat = khat;
+  ctx->khat_key = key;
+  ctx->khat_dirty = false;
+  return MMP_OK;
 }
 
 int validate_terms(mmp_ctx* ctx) {
@@ -338,6 +335,65 @@ int prepare(mmp_ctx* ctx) {
   return MMP_OK;
 }
 
+int upload_table(mmp_ctx* ctx, float2*& dst, const std::vector<float2>& w) {
+  TRY(alloc_into(ctx, dst, w.size() * sizeof(float2)));
+  CK(cudaMemcpy(dst, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice), "upload twiddles");
+  return MMP_OK;
+}
+
+// Whether a launch shape is valid for the context's grid; message in `why`.
+bool shape_ok(const mmp_ctx* ctx, const mmp_shape& s, const char** why) {
+  const Grid& g = ctx->g;
+  FftPlan px, py;
+  if (s.ty != 2 && s.ty != 4 && s.ty != 8) { *why = "ty must be 2, 4 or 8"; return false; }
+  if (s.R != 1 && s.R != 2 && s.R != 4 && s.R != 8) { *why = "R must be 1, 2, 4 or 8"; return false; }
+  if (g.Py % s.R != 0 || (s.R > 1 && g.Py / s.R < 2)) { *why = "R must divide the padded y length"; return false; }
+  if (!make_plan(g.Px, px, s.radix_x) || !make_plan(g.Py / s.R, py, s.radix_y)) {
+    *why = "unsupported FFT plan";
+    return false;
+  }
+  if (passb_smem(g.ny, g.nz, g.Py, g.kzn, s.R, s.stage_kernel != 0).total > 227 * 1024) {
+    *why = "pass B shared memory above 227 KB";
+    return false;
+  }
+  if ((long long)(g.Py / s.R) > (long long)fft_cap(py) * 512) {
+    *why = "pass B column above the FFT capacity of a 512-thread block";
+    return false;
+  }
+  return true;
+}
+
+// Set the launch shape: FFT plans, their twiddle tables, tile rows, cluster
+// size and block sizes.  The cached first stage is dropped (the FP32
+// rounding order changes).
+int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
+  const char* why = "";
+  if (!shape_ok(ctx, s, &why)) return fail(MMP_E_INVAL, "bad shape: %s", why);
+  Grid& g = ctx->g;
+  make_plan(g.Px, ctx->plan_x, s.radix_x);
+  make_plan(g.Py / s.R, ctx->plan_ly, s.radix_y);
+  TRY(upload_table(ctx, ctx->d_tw_x, pass_twiddles(ctx->plan_x)));
+  TRY(upload_table(ctx, ctx->d_tw_ly, pass_twiddles(ctx->plan_ly)));
+  g.ty = s.ty;
+  ctx->R = s.R;
+  ctx->ks = s.stage_kernel != 0;
+  ctx->radix_x = s.radix_x;
+  ctx->radix_y = s.radix_y;
+  launch_threads(g, ctx->R, &ctx->thrA, &ctx->thrB, &ctx->thrC);
+  ctx->k1_valid = false;
+  return MMP_OK;
+}
+
+mmp_shape current_shape(const mmp_ctx* ctx) {
+  mmp_shape s;
+  s.ty = ctx->g.ty;
+  s.radix_x = ctx->radix_x;
+  s.radix_y = ctx->radix_y;
+  s.R = ctx->R;
+  s.stage_kernel = ctx->ks;
+  return s;
+}
+
 DemagArgs demag_args(mmp_ctx* ctx) {
   DemagArgs d;
   d.T = ctx->d_T;
@@ -349,6 +405,7 @@ DemagArgs demag_args(mmp_ctx* ctx) {
   d.plan_x = ctx->plan_x;
   d.plan_ly = ctx->plan_ly;
   d.R = ctx->R;
+  d.ks = ctx->ks;
   return d;
 }
 
@@ -456,7 +513,7 @@ int attempt(mmp_ctx* ctx, double h, bool want_err, int relax, double* err_out, d
   TRY(ensure_k1(ctx, relax));
   if (want_err) CK(cudaMemsetAsync(ctx->d_red, 0, 2 * sizeof(unsigned), ctx->stream), "reset error");
   float ecoef[7];
-  for (int j = 0; j < 7; ++j) ecoef[j] = (float)(h * ((j < 6 ? kA[6][j] : 0.0) - kB4[j]));
+  error_coefs(h, ecoef);
   const float* ek[6];
   for (int j = 0; j < 6; ++j) ek[j] = ctx->d_k[j];
   for (int i = 1; i <= 6; ++i) {
@@ -464,10 +521,8 @@ int attempt(mmp_ctx* ctx, double h, bool want_err, int relax, double* err_out, d
     memset(&sa, 0, sizeof sa);
     sa.y = ctx->d_y;
     sa.nk = i;
-    for (int j = 0; j < i; ++j) {
-      sa.k[j] = ctx->d_k[j];
-      sa.coef[j] = (float)(h * kA[i][j]);
-    }
+    for (int j = 0; j < i; ++j) sa.k[j] = ctx->d_k[j];
+    stage_coefs(h, i, sa.coef);
     sa.normalize = (i == 6);
     bool last = (i == 6);
     TRY(evaluate(ctx, sa, nullptr, ctx->d_k[i], nullptr, last && want_err ? ctx->d_red : nullptr, ecoef, ek,
@@ -492,11 +547,6 @@ void accept(mmp_ctx* ctx, double h) {
   ctx->k1_valid = true;
   ctx->t += h;
   ctx->steps++;
-}
-
-double grow(double err, double tol) {
-  double fac = err == 0.0 ? kGrowMax : kSafety * pow(tol / err, kExponent);
-  return std::min(std::max(fac, kGrowMin), kGrowMax);
 }
 
 // Advance: nsteps attempts-limited loop.  `until` < 0: count accepted steps.
@@ -549,11 +599,48 @@ int advance(mmp_ctx* ctx, long long nsteps, double until, int relax, double torq
   return MMP_OK;
 }
 
+// Device time per pass (ms) of `reps` field evaluations of the current
+// state, from the tracing events (one warm-up evaluation first).
+int time_passes(mmp_ctx* ctx, int reps, double* ta, double* tb, double* tc) {
+  StageArgs sa;
+  memset(&sa, 0, sizeof sa);
+  TRY(evaluate(ctx, sa, ctx->d_y, ctx->d_k[0], nullptr, nullptr, nullptr, nullptr, 0, nullptr));
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  const bool was = ctx->prof;
+  for (int k = 0; k < MMP_NKERNEL; ++k) ctx->prof_used[k] = 0;
+  ctx->prof = true;
+  int rc = MMP_OK;
+  for (int r = 0; r < reps && rc == MMP_OK; ++r)
+    rc = evaluate(ctx, sa, ctx->d_y, ctx->d_k[0], nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+  ctx->prof = was;
+  TRY(rc);
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  double t[3] = {0, 0, 0};
+  const int ks[3] = {MMP_K_PASS_A, MMP_K_PASS_B, MMP_K_FIELD};
+  for (int i = 0; i < 3; ++i) {
+    for (size_t j = 0; j < ctx->prof_used[ks[i]]; ++j) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ctx->prof_events[ks[i]][j].first, ctx->prof_events[ks[i]][j].second),
+         "event time");
+      t[i] += ms;
+    }
+    t[i] /= reps;
+  }
+  for (int k = 0; k < MMP_NKERNEL; ++k) ctx->prof_used[k] = 0;
+  *ta = t[0];
+  *tb = t[1];
+  *tc = t[2];
+  return MMP_OK;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, mmp_shape> g_tuned;
+
 }  // namespace
 
 namespace mmp {
-// Record an error message for mmp_last_error() from another translation unit.
 int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+int ctx_prepare(mmp_ctx* ctx) { return prepare(ctx); }
 }  // namespace mmp
 
 // ============================================================== C-ABI =====
@@ -605,11 +692,6 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
     g.h[a] = (float)ctx->cell[a];
     g.ih[a] = (float)(1.0 / ctx->cell[a]);
   }
-  ctx->R = pick_residues(g);
-  if (ctx->R == 0) { delete ctx; return fail(MMP_E_INVAL, "y-z plane of %d x %d too large for pass B", ny, nz); }
-  bool ok = make_plan(g.Px, ctx->plan_x) && make_plan(g.Py / ctx->R, ctx->plan_ly);
-  if (!ok) { delete ctx; return fail(MMP_E_INVAL, "unsupported FFT length"); }
-  launch_threads(g, ctx->R, &ctx->thrA, &ctx->thrB, &ctx->thrC);
   int rc = MMP_OK;
 #define CR(x) do { if (rc == MMP_OK) rc = (x); } while (0)
   CR(alloc_into(ctx, ctx->d_coef, 2 * MMP_MAX_REGIONS * sizeof(RegionCoef)));
@@ -618,16 +700,18 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
     cudaGetLastError();
     rc = fail(MMP_E_OOM, "pinned allocation failed");
   }
-  auto up = [&](float2*& dst, const std::vector<float2>& w) {
-    if (rc != MMP_OK) return;
-    rc = alloc_into(ctx, dst, w.size() * sizeof(float2));
-    if (rc == MMP_OK)
-      rc = cuda_check(ctx, cudaMemcpy(dst, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice), "twiddles");
-  };
-  up(ctx->d_tw_x, pass_twiddles(ctx->plan_x));
-  up(ctx->d_tw_y, roots(g.Py));
-  up(ctx->d_tw_ly, pass_twiddles(ctx->plan_ly));
-  up(ctx->d_tw_z, roots(g.Pz));
+  CR(upload_table(ctx, ctx->d_tw_y, roots(g.Py)));
+  CR(upload_table(ctx, ctx->d_tw_z, roots(g.Pz)));
+  if (rc == MMP_OK) {
+    mmp_shape sh;
+    sh.ty = pick_tile_rows(g.ny, g.nz);
+    sh.radix_x = 0;
+    sh.radix_y = 0;
+    sh.R = pick_residues(g);
+    sh.stage_kernel = 1;
+    if (sh.R == 0) rc = fail(MMP_E_INVAL, "y-z plane of %d x %d too large for pass B", ny, nz);
+    else rc = apply_shape(ctx, sh);
+  }
 #undef CR
   if (rc == MMP_OK) rc = ensure_state(ctx);
   if (rc != MMP_OK) {
@@ -643,9 +727,9 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
 int mmp_destroy(mmp_ctx* ctx) {
   if (!ctx) return MMP_OK;
   cudaStreamSynchronize(ctx->stream);
+  release_khat(ctx);
   void* bufs[] = {ctx->d_regions, ctx->d_coef, ctx->d_hA, ctx->d_y, ctx->d_stage, ctx->d_B, ctx->d_eps,
-                  ctx->d_sig, ctx->d_T, ctx->d_khat, ctx->d_tw_x, ctx->d_tw_y, ctx->d_tw_ly, ctx->d_tw_z,
-                  ctx->d_red};
+                  ctx->d_sig, ctx->d_T, ctx->d_tw_x, ctx->d_tw_y, ctx->d_tw_ly, ctx->d_tw_z, ctx->d_red};
   for (void* p : bufs) dfree(ctx, p);
   for (int i = 0; i < 7; ++i) dfree(ctx, ctx->d_k[i]);
   if (ctx->h_red) cudaFreeHost(ctx->h_red);
@@ -924,6 +1008,98 @@ int mmp_profile_read(mmp_ctx* ctx, int kernel, long long* launches, double* tota
   }
   if (launches) *launches = (long long)ctx->prof_used[kernel];
   if (total_ms) *total_ms = tot;
+  return MMP_OK;
+}
+
+int mmp_get_shape(mmp_ctx* ctx, mmp_shape* out) {
+  TRY(check_ctx(ctx));
+  if (!out) return fail(MMP_E_INVAL, "out is null");
+  *out = current_shape(ctx);
+  return MMP_OK;
+}
+
+int mmp_set_shape(mmp_ctx* ctx, const mmp_shape* shape) {
+  TRY(check_ctx(ctx));
+  if (!shape) return fail(MMP_E_INVAL, "shape is null");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return apply_shape(ctx, *shape);
+}
+
+int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
+  TRY(check_ctx(ctx));
+  if (flags & ~(MMP_TUNE_BATCH | MMP_TUNE_FORCE)) return fail(MMP_E_INVAL, "unknown flags 0x%x", flags);
+  if (!has(ctx, MMP_T_DEMAG)) return fail(MMP_E_INVAL, "autotune needs the demag term (it tunes the FFT passes)");
+  TRY(prepare(ctx));
+  const bool batch = (flags & MMP_TUNE_BATCH) != 0;
+  const auto key = std::make_tuple(ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->nsub, batch ? 1 : 0);
+  const int reps = 3;
+  double ta = 0, tb = 0, tc = 0;
+  if (!(flags & MMP_TUNE_FORCE)) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      TRY(apply_shape(ctx, it->second));
+      if (chosen) *chosen = it->second;
+      if (eval_ms) {
+        TRY(time_passes(ctx, reps, &ta, &tb, &tc));
+        *eval_ms = ta + tb + tc;
+      }
+      return MMP_OK;
+    }
+  }
+  const char* why = "";
+  mmp_shape best = current_shape(ctx);
+  if (batch) {
+    best.R = 1;
+    best.stage_kernel = 0;
+    if (!shape_ok(ctx, best, &why)) return fail(MMP_E_INVAL, "no batch shape fits this grid: %s", why);
+    TRY(apply_shape(ctx, best));
+  }
+  // passes A and C: tile rows and x plan (pass B fixed)
+  double best_ac = 1e300;
+  mmp_shape base = best;
+  for (int ty : {2, 4, 8})
+    for (int rx = 0; rx < 2; ++rx) {
+      mmp_shape s = base;
+      s.ty = ty;
+      s.radix_x = rx;
+      if (!shape_ok(ctx, s, &why)) continue;
+      TRY(apply_shape(ctx, s));
+      TRY(time_passes(ctx, reps, &ta, &tb, &tc));
+      if (ta + tc < best_ac) {
+        best_ac = ta + tc;
+        best.ty = ty;
+        best.radix_x = rx;
+      }
+    }
+  // pass B: residue classes, kernel staging and y plan
+  double best_b = 1e300;
+  base = best;
+  for (int R : {1, 2, 4, 8})
+    for (int st = 0; st < 2; ++st)
+      for (int ry = 0; ry < 2; ++ry) {
+        if (batch && (R != 1 || st != 0)) continue;
+        mmp_shape s = base;
+        s.R = R;
+        s.stage_kernel = st;
+        s.radix_y = ry;
+        if (!shape_ok(ctx, s, &why)) continue;
+        TRY(apply_shape(ctx, s));
+        TRY(time_passes(ctx, reps, &ta, &tb, &tc));
+        if (tb < best_b) {
+          best_b = tb;
+          best.R = R;
+          best.stage_kernel = st;
+          best.radix_y = ry;
+        }
+      }
+  TRY(apply_shape(ctx, best));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+  }
+  if (chosen) *chosen = best;
+  if (eval_ms) *eval_ms = best_ac + best_b;
   return MMP_OK;
 }
 

@@ -27,7 +27,7 @@
 
 namespace mmp {
 int report_error(int code, const char* msg);
-}
+}  // namespace mmp
 
 using namespace mmp;
 

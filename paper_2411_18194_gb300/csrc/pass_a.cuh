@@ -1,0 +1,123 @@
+// pass_a.cuh -- device body of pass A of the demag convolution: the
+// Dormand-Prince stage assembly fused into the forward FFT along x of
+// M = sum_s Ms m_s (two real rows per complex transform; the zero padding
+// x >= nx is never loaded).  Used by the per-context kernel (pass_a.cu) and
+// the batched stage kernel (batch.cu).
+#pragma once
+#include "kernels.h"
+
+namespace mmp {
+
+// ------------------------------------------------------------- pass A ----
+// Shared memory: the row-pair FFT buffer (padded layout), the length-Px
+// twiddles, and for the renormalised stage 1/|m_i| of every tile cell and
+// sublattice.
+__host__ __device__ __forceinline__ size_t passa_twiddle_offset(int Px, int ty) {
+  return (size_t)(ty >> 1) * fft_pitch(Px) * sizeof(float2);
+}
+__host__ __device__ __forceinline__ size_t passa_inv_offset(int Px, int ty) {
+  return passa_twiddle_offset(Px, ty) + (size_t)Px * sizeof(float2);
+}
+
+// Stage value of component c of part p at a cell: assembled from y and the
+// previous stages (ASSEMBLE) or read from the given stage state.
+template <bool ASSEMBLE>
+__device__ __forceinline__ float stage_value(const StageArgs& a, long long n, int p, int c, long long cell) {
+  const long long idx = (long long)(3 * p + c) * n + cell;
+  if (!ASSEMBLE) return a.stage[idx];
+  float acc = a.y[idx];
+#pragma unroll
+  for (int j = 0; j < 7; ++j)
+    if (j < a.nk) acc = fmaf(a.coef[j], a.k[j][idx], acc);
+  return acc;
+}
+
+// One component of pass A: the stage values of component c are assembled
+// straight into the FFT input (and written to the stage state once), M_c is
+// packed in row pairs, transformed, and the unpacked half spectra are
+// written to T.  Called three times in straight-line code (a loop over c
+// made the compiler keep the FFT pass registers in local memory).
+template <int NSUB, bool ASSEMBLE>
+__device__ __forceinline__ void passA_component(int c, float2* fbuf, const float2* tw, const float* inv,
+                                                const Grid& g, const StageArgs& a, const DemagArgs& d,
+                                                const Coefs& co, int z, int y0) {
+  const int nx = g.nx, ny = g.ny, Px = g.Px;
+  const int pitch = fft_pitch(Px);
+  const long long n = g.n;
+  for (int e = threadIdx.x; e < (g.ty >> 1) * Px; e += blockDim.x) {
+    int p = e / Px, x = e - p * Px;
+    float v2[2] = {0.0f, 0.0f};
+    if (x < nx) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = 2 * p + h, y = y0 + row;
+        if (y >= ny) continue;
+        const long long cell = x + (long long)nx * (y + (long long)ny * z);
+        const int reg = co.uniform ? 0 : co.regions[cell];
+#pragma unroll
+        for (int s = 0; s < NSUB; ++s) {
+          float m = stage_value<ASSEMBLE>(a, n, s, c, cell);
+          if (ASSEMBLE) {
+            if (a.normalize) m *= inv[(s * g.ty + row) * nx + x];
+            a.stage[(long long)(3 * s + c) * n + cell] = m;
+          }
+          v2[h] = fmaf(co.reg[s * MMP_MAX_REGIONS + reg].ms, m, v2[h]);
+        }
+      }
+    }
+    fbuf[fidx(p, x, pitch)] = make_float2(v2[0], v2[1]);
+  }
+  __syncthreads();
+  block_fft<false>(fbuf, d.plan_x, (g.ty >> 1), tw);
+  for (int e = threadIdx.x; e < g.kxn * g.ty; e += blockDim.x) {
+    int k = e / g.ty, row = e - k * g.ty, y = y0 + row;
+    if (y >= ny) continue;
+    int p = row >> 1;
+    float2 Z = fbuf[fidx(p, k, pitch)];
+    float2 Zm = fbuf[fidx(p, k == 0 ? 0 : Px - k, pitch)];
+    float2 X;
+    if ((row & 1) == 0) X = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+    else X = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
+    d.T[(((long long)k * 3 + c) * g.nz + z) * ny + y] = X;
+  }
+  __syncthreads();
+}
+
+// Pass A of one tile: rows y0 .. y0 + ty - 1 of plane z.  `sraw` is the
+// block's dynamic shared memory.
+template <int NSUB, bool ASSEMBLE>
+__device__ __forceinline__ void passA_tile(unsigned char* sraw, const Grid& g, const StageArgs& a,
+                                           const DemagArgs& d, const Coefs& co, int z, int y0) {
+  const int Px = g.Px, nx = g.nx, ny = g.ny;
+  float2* fbuf = reinterpret_cast<float2*>(sraw);
+  float2* tw = reinterpret_cast<float2*>(sraw + passa_twiddle_offset(Px, g.ty));
+  float* inv = reinterpret_cast<float*>(sraw + passa_inv_offset(Px, g.ty));
+  const long long n = g.n;
+  for (int i = threadIdx.x; i < Px; i += blockDim.x) tw[i] = __ldg(d.tw_x + i);
+  if (ASSEMBLE && (a.normalize || a.nparts > a.nsub)) {
+    for (int e = threadIdx.x; e < g.ty * nx; e += blockDim.x) {
+      int row = e / nx, x = e - row * nx, y = y0 + row;
+      if (y >= ny) continue;
+      const long long cell = x + (long long)nx * (y + (long long)ny * z);
+      if (a.normalize) {
+        // 1/|m_i| of the renormalised stage, per sublattice
+        for (int s = 0; s < NSUB; ++s) {
+          float v0 = stage_value<true>(a, n, s, 0, cell);
+          float v1 = stage_value<true>(a, n, s, 1, cell);
+          float v2 = stage_value<true>(a, n, s, 2, cell);
+          float nn = v0 * v0 + v1 * v1 + v2 * v2;
+          inv[(s * g.ty + row) * nx + x] = nn > 0.0f ? rnorm3df(v0, v1, v2) : 1.0f;
+        }
+      }
+      // elastic parts (u, v): assembled here, not transformed
+      for (int p = a.nsub; p < a.nparts; ++p)
+        for (int c = 0; c < 3; ++c) a.stage[(long long)(3 * p + c) * n + cell] = stage_value<true>(a, n, p, c, cell);
+    }
+  }
+  __syncthreads();
+  passA_component<NSUB, ASSEMBLE>(0, fbuf, tw, inv, g, a, d, co, z, y0);
+  passA_component<NSUB, ASSEMBLE>(1, fbuf, tw, inv, g, a, d, co, z, y0);
+  passA_component<NSUB, ASSEMBLE>(2, fbuf, tw, inv, g, a, d, co, z, y0);
+}
+
+}  // namespace mmp

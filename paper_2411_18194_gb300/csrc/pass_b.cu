@@ -1,274 +1,28 @@
-// pass_b.cu -- pass B of the demag convolution, per kx plane: the ky
-// residue class r (mod R) of the zero-padded y transform as a folded
-// length-Py/R FFT, the z transform + 3x3 symmetric demag-kernel multiply +
-// inverse z transform in registers, the inverse y FFT, and the
-// recombination of the R classes through distributed shared memory of an
-// R-CTA thread-block cluster (only y < ny is formed).
-//
-// Shared memory per CTA: the 3 nz columns (padded FFT layout), the
-// Stockham twiddles of length Py/R, the fold and recombination twiddles of
-// this residue class, and this CTA's slice of the kernel octant, which is
-// prefetched with cp.async while the fold and the forward FFT run.
+// pass_b.cu -- pass B of the demag convolution (body in pass_b.cuh): the
+// per-context kernel, launched as clusters of R CTAs per kx plane.
 #include <cooperative_groups.h>
 #include "kernels.h"
 #include "launch.cuh"
 #include "stage.cuh"
-
-namespace cg = cooperative_groups;
+#include "pass_b.cuh"
 
 namespace mmp {
 
-// ------------------------------------------------------------- helpers ----
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// 3x3 symmetric kernel times a complex 3-vector.  K points at the six
-// components (xx, yy, zz, xy, xz, yz) of octant entry (|ky|, |kz|); sy, sz
-// flip the components odd in ky, kz.
-__device__ __forceinline__ void kmul(const float* K, float sy, float sz, float2& a, float2& b, float2& c) {
-  const float2 k01 = reinterpret_cast<const float2*>(K)[0];
-  const float2 k23 = reinterpret_cast<const float2*>(K)[1];
-  const float2 k45 = reinterpret_cast<const float2*>(K)[2];
-  float xx = k01.x, yy = k01.y, zz = k23.x, xy = k23.y * sy, xz = k45.x * sz, yz = k45.y * sy * sz;
-  float2 ha = make_float2(xx * a.x + xy * b.x + xz * c.x, xx * a.y + xy * b.y + xz * c.y);
-  float2 hb = make_float2(xy * a.x + yy * b.x + yz * c.x, xy * a.y + yy * b.y + yz * c.y);
-  float2 hc = make_float2(xz * a.x + yz * b.x + zz * c.x, xz * a.y + yz * b.y + zz * c.y);
-  a = ha; b = hb; c = hc;
-}
-
-template <int N, bool INV>
-__device__ __forceinline__ void dft_small(float2 (&f)[N]) {
-  if constexpr (N == 2) dft2<INV>(f[0], f[1]);
-  else if constexpr (N == 4) dft4<INV>(f[0], f[1], f[2], f[3]);
-  else dft8<INV>(f);
-}
-
-// nz = 1: the kernel multiply alone, one thread per column.
-__device__ __forceinline__ void zkz_single(float2* W, int pitch, int kp, const float* Kc, float sy) {
-  float2 a = W[fidx(0, kp, pitch)], b = W[fidx(1, kp, pitch)], c = W[fidx(2, kp, pitch)];
-  kmul(Kc, sy, 1.0f, a, b, c);
-  W[fidx(0, kp, pitch)] = a; W[fidx(1, kp, pitch)] = b; W[fidx(2, kp, pitch)] = c;
-}
-
-// nz = NZ in {2, 4, 8} (Pz = 2 NZ): two lanes per ky column, lane parity
-// `par` handles kz of that parity:  F[2q+par] = DFT_NZ(v[z] w^(par z))[q],
-// multiply, inverse DFT_NZ, times w^(-par z); the two lanes add their halves
-// through a shuffle and each writes NZ/2 of the z outputs.  Both lanes read
-// the column before the shuffle, so neither writes before the other read.
-template <int NZ>
-__device__ __forceinline__ void zkz_pair(float2* W, int pitch, int kp, bool valid, int par, const float* Kc,
-                                         float sy, const float2* __restrict__ twz) {
-  float2 f[3][NZ];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int z = 0; z < NZ; ++z) {
-      float2 v = valid ? W[fidx(c * NZ + z, kp, pitch)] : make_float2(0.0f, 0.0f);
-      f[c][z] = par ? cmul(v, __ldg(twz + z)) : v;
-    }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) dft_small<NZ, false>(f[c]);
-#pragma unroll
-  for (int q = 0; q < NZ; ++q) {
-    int kz = 2 * q + par;
-    int ikz = kz <= NZ ? kz : 2 * NZ - kz;
-    float sz = kz <= NZ ? 1.0f : -1.0f;
-    kmul(Kc + ikz * 6, sy, sz, f[0][q], f[1][q], f[2][q]);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) dft_small<NZ, true>(f[c]);
-  if (par) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int z = 0; z < NZ; ++z) f[c][z] = cmul(f[c][z], cconj(__ldg(twz + z)));
-  }
-  constexpr int H = NZ / 2;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int z = 0; z < H; ++z) {
-      float2 send = par ? f[c][z] : f[c][z + H];
-      float2 keep = par ? f[c][z + H] : f[c][z];
-      float2 recv;
-      recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
-      recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
-      if (valid) W[fidx(c * NZ + z + (par ? H : 0), kp, pitch)] = cadd(keep, recv);
-    }
-}
-
-// Any nz <= 16: direct DFT over the padded length Pz, one thread per column.
-__device__ void zkz_generic(float2* W, int kp, int pitch, int nz, int Pz, const float* Kc, float sy,
-                            const float2* __restrict__ twz) {
-  float2 out[3][16];
-  for (int c = 0; c < 3; ++c)
-    for (int zz = 0; zz < 16; ++zz) out[c][zz] = make_float2(0.0f, 0.0f);
-  for (int kz = 0; kz < Pz; ++kz) {
-    float2 F[3];
-    for (int c = 0; c < 3; ++c) {
-      float2 acc = make_float2(0.0f, 0.0f);
-      for (int zz = 0; zz < nz; ++zz)
-        acc = cadd(acc, cmul(W[fidx(c * nz + zz, kp, pitch)], __ldg(twz + (kz * zz) % Pz)));
-      F[c] = acc;
-    }
-    int ikz = kz <= Pz / 2 ? kz : Pz - kz;
-    float sz = kz <= Pz / 2 ? 1.0f : -1.0f;
-    kmul(Kc + ikz * 6, sy, sz, F[0], F[1], F[2]);
-    for (int zz = 0; zz < nz; ++zz) {
-      float2 w = cconj(__ldg(twz + (kz * zz) % Pz));
-      for (int c = 0; c < 3; ++c) out[c][zz] = cadd(out[c][zz], cmul(F[c], w));
-    }
-  }
-  for (int c = 0; c < 3; ++c)
-    for (int zz = 0; zz < nz; ++zz) W[fidx(c * nz + zz, kp, pitch)] = out[c][zz];
-}
-
-template <int NZ>
+template <int NZ, bool KS>
 __global__ void __launch_bounds__(512) k_passB(Grid g, DemagArgs d) {
   extern __shared__ __align__(16) unsigned char sraw[];
-  const int R = d.R;                 // cluster size = residue classes of ky
-  const int r = (int)(blockIdx.x % R);
-  const int kx = blockIdx.y;
-  const int ny = g.ny, nz = g.nz, Py = g.Py, kzn = g.kzn;
-  const int Ly = Py / R;
-  const int pitch = fft_pitch(Ly);
-  const int ncol = 3 * nz;
-  const PassBSmem L = passb_smem(ny, nz, Py, kzn, R);
-  float2* W = reinterpret_cast<float2*>(sraw);
-  float2* twl = reinterpret_cast<float2*>(sraw + L.twl);
-  float2* twf = reinterpret_cast<float2*>(sraw + L.twf);
-  float2* twc = reinterpret_cast<float2*>(sraw + L.twc);
-  float* Ks = reinterpret_cast<float*>(sraw + L.ks);
-  float2* Tk = d.T + (long long)kx * ncol * ny;
-
-  // 0. prefetch this CTA's kernel rows (|ky| of ky = R k' + r) asynchronously
-  const int krow = g.krow;
-  {
-    const float* kbase = d.khat + (long long)kx * g.kyn * krow;
-    for (int kp = threadIdx.x; kp < Ly; kp += blockDim.x) {
-      int ky = R * kp + r;
-      int iky = ky <= Py / 2 ? ky : Py - ky;
-      const float4* src = reinterpret_cast<const float4*>(kbase + (long long)iky * krow);
-      float4* dst = reinterpret_cast<float4*>(Ks + kp * krow);
-      for (int w = 0; w < (krow >> 2); ++w) cp_async16(dst + w, src + w);
-    }
-    cp_async_commit();
-  }
-  // 1. twiddles: Stockham (pass-ordered, length Ly), fold w^(r j), recombination w^y
-  const int ylo = (int)((long long)ny * r / R), yhi = (int)((long long)ny * (r + 1) / R);
-  const int cnt = yhi - ylo;
-  for (int i = threadIdx.x; i < Ly; i += blockDim.x) {
-    twl[i] = __ldg(d.tw_ly + i);
-    twf[i] = __ldg(d.tw_y + r * i);
-  }
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) twc[i] = __ldg(d.tw_y + ylo + i);
-  __syncthreads();
-  // 2. fold the ky residue class r: g_r[j] = w^(r j) sum_q T[j + q Ly] w_R^(r q).
-  // Four columns per step keep several independent loads in flight.
-  for (int col0 = 0; col0 < ncol; col0 += 4) {
-    for (int j = threadIdx.x; j < Ly; j += blockDim.x) {
-      float2 acc[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        acc[u] = (col0 + u < ncol && j < ny) ? Tk[(long long)(col0 + u) * ny + j] : make_float2(0.0f, 0.0f);
-      int tq = 0;
-      for (int y = j + Ly; y < ny; y += Ly) {
-        tq += r;
-        if (tq >= R) tq -= R;
-        const float2 ph = __ldg(d.tw_y + tq * Ly);
-        float2 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          v[u] = col0 + u < ncol ? Tk[(long long)(col0 + u) * ny + y] : make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = cadd(acc[u], cmul(v[u], ph));
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (col0 + u < ncol) W[fidx(col0 + u, j, pitch)] = r > 0 ? cmul(acc[u], twf[j]) : acc[u];
-    }
-  }
-  __syncthreads();
-  block_fft<false>(W, d.plan_ly, ncol, twl);
-  cp_async_wait_all();
-  __syncthreads();
-  // 3. z transform + kernel multiply + inverse z transform per ky column
-  if constexpr (NZ == 1) {
-    for (int kp = threadIdx.x; kp < Ly; kp += blockDim.x) {
-      int ky = R * kp + r;
-      zkz_single(W, pitch, kp, Ks + kp * krow, ky <= Py / 2 ? 1.0f : -1.0f);
-    }
-  } else if constexpr (NZ > 1) {
-    const int half = blockDim.x >> 1;
-    for (int base = 0; base < Ly; base += half) {
-      int kp = base + (threadIdx.x >> 1);
-      bool valid = kp < Ly;
-      int ky = R * kp + r;
-      zkz_pair<NZ>(W, pitch, valid ? kp : 0, valid, threadIdx.x & 1, Ks + (valid ? kp : 0) * krow,
-                   ky <= Py / 2 ? 1.0f : -1.0f, d.tw_z);
-    }
-  } else {
-    for (int kp = threadIdx.x; kp < Ly; kp += blockDim.x) {
-      int ky = R * kp + r;
-      zkz_generic(W, kp, pitch, nz, g.Pz, Ks + kp * krow, ky <= Py / 2 ? 1.0f : -1.0f, d.tw_z);
-    }
-  }
-  __syncthreads();
-  block_fft<true>(W, d.plan_ly, ncol, twl);
-  // 4. recombine: out[y] = sum_q w^(-q y) h_q[y mod Ly], y < ny
-  if (R == 1) {
-    for (int e = threadIdx.x; e < ncol * ny; e += blockDim.x) {
-      int col = e / ny, y = e - col * ny;
-      Tk[e] = W[fidx(col, y, pitch)];
-    }
-  } else {
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
-    for (int col0 = 0; col0 < ncol; col0 += 4) {
-      for (int yi = threadIdx.x; yi < cnt; yi += blockDim.x) {
-        const int y = ylo + yi;
-        int j = y;
-        while (j >= Ly) j -= Ly;
-        const float2 w1 = cconj(twc[yi]);   // w^(-y)
-        float2 acc[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float2* W0 = cl.map_shared_rank(W, 0);
-          acc[u] = col0 + u < ncol ? W0[fidx(col0 + u, j, pitch)] : make_float2(0.0f, 0.0f);
-        }
-        float2 wq = w1;
-        for (int q = 1; q < R; ++q) {
-          float2 v[4];
-          const float2* Wr = cl.map_shared_rank(W, q);
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            v[u] = col0 + u < ncol ? Wr[fidx(col0 + u, j, pitch)] : make_float2(0.0f, 0.0f);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = cadd(acc[u], cmul(v[u], wq));
-          wq = cmul(wq, w1);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (col0 + u < ncol) Tk[(long long)(col0 + u) * ny + y] = acc[u];
-      }
-    }
-    cl.sync();
-  }
+  passB_plane<NZ, KS>(sraw, g, d, blockIdx.y, (int)(blockIdx.x % d.R));
 }
 
-size_t smem_passB(const Grid& g, int R) { return passb_smem(g.ny, g.nz, g.Py, g.kzn, R).total; }
+size_t smem_passB(const Grid& g, int R, bool ks) { return passb_smem(g.ny, g.nz, g.Py, g.kzn, R, ks).total; }
 
-template <int NZ>
-static cudaError_t launch_passB_t(const Grid& g, const DemagArgs& d, int threads, cudaStream_t s) {
-  size_t sm = smem_passB(g, d.R);
-  cudaError_t e = set_smem(k_passB<NZ>, sm);
+template <int NZ, bool KS>
+static cudaError_t launch_passB_k(const Grid& g, const DemagArgs& d, int threads, cudaStream_t s) {
+  size_t sm = smem_passB(g, d.R, KS);
+  cudaError_t e = set_smem(k_passB<NZ, KS>, sm);
   if (e != cudaSuccess) return e;
   if (d.R == 1) {
-    k_passB<NZ><<<dim3(1, g.kxn), threads, sm, s>>>(g, d);
+    k_passB<NZ, KS><<<dim3(1, g.kxn), threads, sm, s>>>(g, d);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -283,7 +37,12 @@ static cudaError_t launch_passB_t(const Grid& g, const DemagArgs& d, int threads
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_passB<NZ>, g, d);
+  return cudaLaunchKernelEx(&cfg, k_passB<NZ, KS>, g, d);
+}
+
+template <int NZ>
+static cudaError_t launch_passB_t(const Grid& g, const DemagArgs& d, int threads, cudaStream_t s) {
+  return d.ks ? launch_passB_k<NZ, true>(g, d, threads, s) : launch_passB_k<NZ, false>(g, d, threads, s);
 }
 
 cudaError_t launch_passB(const Grid& g, const DemagArgs& d, int threads, cudaStream_t s) {

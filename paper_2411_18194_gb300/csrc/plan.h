@@ -21,17 +21,43 @@ inline int nice_length(int n) {
   return best;
 }
 
-inline bool make_plan(int L, FftPlan& p) {
+// Radix plan of length L = 2^a 3^b.  variant 0: as many radix-16 passes as
+// possible (then one 8, 4 or 2); variant 1: radix-8 passes (then one 4 or
+// 2).  Both are exact; they differ in FP32 rounding order and speed.
+inline bool make_plan(int L, FftPlan& p, int variant = 0) {
   p.L = L;
   p.n16 = p.n8 = p.n4 = p.n2 = p.n3 = 0;
   int r = L, a = 0;
   while (r % 3 == 0) { r /= 3; p.n3++; }
   while (r % 2 == 0) { r /= 2; a++; }
-  if (r != 1) return false;
-  p.n16 = a / 4;
-  p.n8 = (a % 4) == 3;
-  p.n4 = (a % 4) == 2;
-  p.n2 = (a % 4) == 1;
+  if (r != 1 || variant < 0 || variant > 1) return false;
+  if (variant == 0) {
+    p.n16 = a / 4;
+    p.n8 = (a % 4) == 3;
+    p.n4 = (a % 4) == 2;
+    p.n2 = (a % 4) == 1;
+  } else {
+    p.n8 = a / 3;
+    p.n4 = (a % 3) == 2;
+    p.n2 = (a % 3) == 1;
+  }
+  // uniform-stride addressing of stockham_pass: loads need L/R a multiple
+  // of 16 (or the transform within 16), stores Ns a multiple of 16 (or a
+  // power-of-two radix with R Ns <= 16)
+  p.lin = 1;
+  int Ns = 1;
+  auto check = [&](int R) {
+    const int nbf = L / R;
+    const bool ld = nbf % 16 == 0 || R * nbf <= 16;
+    const bool st = Ns % 16 == 0 || ((R & (R - 1)) == 0 && R * Ns <= 16);
+    if (!ld || !st) p.lin = 0;
+    Ns *= R;
+  };
+  for (int s = 0; s < p.n16; ++s) check(16);
+  for (int s = 0; s < p.n8; ++s) check(8);
+  if (p.n4) check(4);
+  if (p.n2) check(2);
+  for (int s = 0; s < p.n3; ++s) check(3);
   return true;
 }
 
@@ -53,12 +79,20 @@ inline std::vector<float2> pass_twiddles(const FftPlan& p) {
     Ns *= R;
   };
   for (int s = 0; s < p.n16; ++s) add(16);
-  if (p.n8) add(8);
+  for (int s = 0; s < p.n8; ++s) add(8);
   if (p.n4) add(4);
   if (p.n2) add(2);
   for (int s = 0; s < p.n3; ++s) add(3);
   while ((int)w.size() < p.L) w.push_back(make_float2(1.0f, 0.0f));
   return w;
+}
+
+// Complex values one thread holds in a pass of block_fft<.., 32>: 32, but
+// 30 for plans with a radix-3 pass (10 butterflies of 3).
+inline int fft_cap(const FftPlan& p) { return p.n3 ? 30 : 32; }
+inline int fft_cap(int L) {
+  FftPlan p;
+  return make_plan(L, p) ? fft_cap(p) : 32;
 }
 
 inline std::vector<float2> roots(int P) {
@@ -72,14 +106,14 @@ inline std::vector<float2> roots(int P) {
 
 // Residue classes of ky per pass-B cluster: the smallest power of two
 // (<= 8) whose CTA shared memory (columns, twiddles, kernel slice) fits in
-// the 227 KB a block may use, with at most 32 FFT elements per thread of a
-// 512-thread block.  0 when none fits.
+// the 227 KB a block may use, with the FFT elements within what a
+// 512-thread block holds (fft_cap per thread).  0 when none fits.
 inline int pick_residues(const Grid& g) {
   for (int R = 1; R <= 8; R *= 2) {
     if (g.Py % R != 0 || (R > 1 && g.Py / R < 2)) break;
-    size_t sm = passb_smem(g.ny, g.nz, g.Py, g.kzn, R).total;
+    size_t sm = passb_smem(g.ny, g.nz, g.Py, g.kzn, R, true).total;
     long long el = (long long)3 * g.nz * (g.Py / R);
-    if (sm <= 227 * 1024 && el <= 32LL * 512) return R;
+    if (sm <= 227 * 1024 && el <= (long long)fft_cap(g.Py / R) * 512) return R;
   }
   return 0;
 }
@@ -92,14 +126,18 @@ inline int pick_tile_rows(int ny, int nz) {
   return ty;
 }
 
-// Block sizes of passes A, B and C (at most 32 FFT elements per thread).
+// Block sizes of passes A, B and C (at most fft_cap FFT elements per
+// thread; pick_residues and the x-length limit keep them within 512).
 inline void launch_threads(const Grid& g, int R, int* thrA, int* thrB, int* thrC) {
   auto r32 = [](long long v) { return (int)((v + 31) / 32 * 32); };
+  auto need = [](long long el, int cap) { return (el + cap - 1) / cap; };
   const int np = g.ty >> 1;
-  *thrA = std::min(512, std::max(128, r32((long long)np * g.Px / 32)));
-  long long elB = (long long)3 * g.nz * (g.Py / R);
-  *thrB = std::min(512, std::max(64, r32(std::max(elB / 32, (long long)(g.Py / R)))));
-  *thrC = std::min(512, std::max(std::max(128, r32((long long)np * g.Px / 32)), r32((long long)g.ty * g.nx / 8)));
+  const long long fx = need((long long)np * g.Px, fft_cap(g.Px));
+  *thrA = std::min(512, std::max(128, r32(fx)));
+  const int Ly = g.Py / R;
+  const long long elB = (long long)3 * g.nz * Ly;
+  *thrB = std::min(512, std::max(64, r32(std::max(need(elB, fft_cap(Ly)), (long long)Ly))));
+  *thrC = std::min(512, std::max(std::max(128, r32(fx)), r32((long long)g.ty * g.nx / 8)));
 }
 
 }  // namespace mmp

@@ -1,0 +1,199 @@
+"""Continuous-batching server of relaxation solves on one GPU.
+
+Requests (a magnet, its initial state and a relax goal) arrive over time.
+The server admits them in arrival order while a device-memory budget
+allows, adds each admitted context to one mmp_batch, and advances the batch
+a few lock-step attempts at a time, so a request that arrives while others
+are on the GPU joins at the next lock step and its work overlaps theirs.
+Finished members leave the batch and free their memory.  All arithmetic
+runs in libmmp (mmp_batch_advance); this module is host bookkeeping only.
+
+A member computes exactly what the same context computes alone (same shape,
+same FP32 stage coefficients, same FP64 step control), so a request's result
+is bitwise the same in the mix and served by itself.
+
+Memory accounting per request (bytes, FP32 state): the state, six stage
+vectors and the stage buffer (9 x 12 B per cell), the x-transformed spectrum
+(3 nz ny (Px/2 + 1) complex64), the coefficient table, and for a grid whose
+demag kernel spectrum is not yet resident, the spectrum (shared by requests
+of the same grid and cell size) plus its FP64 build buffers while it is
+built.
+"""
+import collections
+import time
+
+import numpy as np
+
+from .binding import Batch, Magnet
+
+
+def _nice(n):
+    """Padded FFT length of the library: the smallest even 2^a or 3 * 2^a
+    at least 2n - 1 (1 when n = 1)."""
+    if n == 1:
+        return 1
+    p2, p3 = 2, 6
+    while p2 < 2 * n - 1:
+        p2 *= 2
+    while p3 < 2 * n - 1:
+        p3 *= 2
+    return min(p2, p3)
+
+
+def request_bytes(shape, spectrum_resident):
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    Px, Py, Pz = _nice(nx), _nice(ny), _nice(nz)
+    kxn, kyn, kzn = Px // 2 + 1, Py // 2 + 1, Pz // 2 + 1
+    krow = (6 * kzn + 3) // 4 * 4
+    b = 9 * 12 * n + 3 * nz * ny * kxn * 8 + 2 * 256 * 160 + 64 * 1024
+    if not spectrum_resident:
+        ext = max(n, kxn * ny * nz, kxn * kyn * nz, kxn * kyn * kzn)
+        b += kxn * kyn * krow * 4 + 2 * 6 * 8 * ext
+    return b
+
+
+class Request:
+    def __init__(self, rid, workload, arrival, torque_tol, max_time):
+        self.id = rid
+        self.workload = workload
+        self.arrival = float(arrival)
+        self.torque_tol = float(torque_tol)
+        self.max_time = float(max_time)
+        self.admitted = None
+        self.done = None
+        self.status = None
+        self.mag = None
+        self.bytes = 0
+        self.result = None
+
+    @property
+    def latency(self):
+        return None if self.done is None else self.done - self.arrival
+
+
+def _make_magnet(w, dt0):
+    import torch
+    mag = Magnet.from_problem(w.problem)
+    mag.set_m(0, torch.from_numpy(np.ascontiguousarray(w.m0[0])).cuda())
+    mag.set_solver(adaptive=True, dt=dt0, tol=w.tol, dt_min=w.dt_min, dt_max=w.dt_max)
+    mag.autotune(batch=True)          # cached per geometry: the batch shape
+    return mag
+
+
+class RelaxServer:
+    """Admission by memory budget + continuous batching of relax solves."""
+
+    def __init__(self, budget_bytes=150e9, attempts_per_round=4, dt0=1e-14, keep_results=False):
+        self.budget = float(budget_bytes)
+        self.attempts = int(attempts_per_round)
+        self.dt0 = float(dt0)
+        self.keep = keep_results
+        self.batch = Batch()
+        self.queue = collections.deque()
+        self.active = []
+        self.finished = []
+        self.used = 0.0
+        self.spectra = collections.Counter()      # (shape, cell) -> resident users
+        self.peak_members = 0
+
+    def submit(self, req):
+        self.queue.append(req)
+
+    def _key(self, req):
+        p = req.workload.problem
+        return (tuple(p.shape), tuple(p.cell))
+
+    def _admit(self, now):
+        while self.queue and self.queue[0].arrival <= now:
+            req = self.queue[0]
+            need = request_bytes(req.workload.problem.shape, self.spectra[self._key(req)] > 0)
+            if self.active and self.used + need > self.budget:
+                break                                  # wait for memory (FIFO)
+            self.queue.popleft()
+            req.mag = _make_magnet(req.workload, self.dt0)
+            req.bytes = need
+            self.used += need
+            self.spectra[self._key(req)] += 1
+            self.batch.add(req.mag, "relax", req.torque_tol, req.max_time)
+            req.admitted = now
+            self.active.append(req)
+        self.peak_members = max(self.peak_members, len(self.active))
+
+    def _retire(self, now):
+        keep = []
+        for req in self.active:
+            done, status = self.batch.status(req.mag)
+            if not done:
+                keep.append(req)
+                continue
+            self.batch.remove(req.mag)
+            req.done = now
+            req.status = status
+            if self.keep:
+                req.result = _read_m(req.mag)
+            req.mag.close()
+            req.mag = None
+            self.used -= req.bytes
+            self.spectra[self._key(req)] -= 1
+            self.finished.append(req)
+        self.active = keep
+
+    def run(self, requests, clock=time.perf_counter):
+        """Serve `requests` (arrival times relative to the start) in real
+        time; returns them with admitted/done times filled in."""
+        for r in sorted(requests, key=lambda r: r.arrival):
+            self.submit(r)
+        t0 = clock()
+        while self.queue or self.active:
+            now = clock() - t0
+            self._admit(now)
+            if not self.active:
+                time.sleep(max(0.0, min(0.01, self.queue[0].arrival - now)))
+                continue
+            self.batch.advance(self.attempts)
+            self._retire(clock() - t0)
+        return self.finished
+
+    def close(self):
+        for req in self.active:
+            self.batch.remove(req.mag)
+            req.mag.close()
+        self.active = []
+        self.batch.close()
+
+
+def _read_m(mag):
+    import torch
+    nx, ny, nz = mag.shape
+    out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    mag.get_m(0, out)
+    return out.cpu().numpy()
+
+
+def serve_one_at_a_time(requests, dt0=1e-14, keep_results=False, clock=time.perf_counter):
+    """The plain path: each request relaxed alone (mmp_relax) in arrival
+    order, the next one starting when the previous has finished."""
+    t0 = clock()
+    out = []
+    for req in sorted(requests, key=lambda r: r.arrival):
+        now = clock() - t0
+        if now < req.arrival:
+            time.sleep(req.arrival - now)
+        req.admitted = clock() - t0
+        mag = _make_magnet(req.workload, dt0)
+        mag.relax(torque_tol=req.torque_tol, max_time=req.max_time)
+        if keep_results:
+            req.result = _read_m(mag)
+        mag.close()
+        req.done = clock() - t0
+        req.status = 0
+        out.append(req)
+    return out
+
+
+def latency_stats(reqs):
+    lat = np.array([r.latency for r in reqs], dtype=np.float64)
+    span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    return {"solves": len(reqs), "solves_per_s": len(reqs) / span, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "span_s": span}

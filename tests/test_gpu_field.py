@@ -8,7 +8,7 @@ regions with empty cells, and the two-sublattice magnetoelastic path."""
 import numpy as np
 import pytest
 
-from inputs import config_small
+from inputs import MU0, config_small, random_unit_vectors
 from gpu_util import field_tolerance, torque_tolerance, make_magnet, gpu_eval, oracle_eval
 
 pytestmark = pytest.mark.gpu
@@ -83,3 +83,33 @@ def test_large_random_exchange_field_within_bar():
     assert np.abs(Bo[0]).max() > 100.0
     assert np.abs(Bg[0] - Bo[0]).max() <= bar
     mag.close()
+
+
+def test_radix3_x_length_at_full_tile_capacity():
+    """nx = 1025 pads to Px = 3072 = 3 * 2^10; with ny = 152, nz = 16 the tile
+    holds 8 rows, so pass A/C transform 4 row pairs of 3072 points: 12288
+    values, more than 30 per thread of a 384-thread block (the radix-3 pass
+    holds 10 butterflies of 3 per thread).  Sampled cells against the
+    oracle's direct sum of the demag definition plus its local terms."""
+    from oracle import demag, fields
+    from inputs import Problem
+    p = Problem((1025, 152, 16), (3e-9, 3e-9, 2e-9), 1, frozenset({"DEMAG", "EXCH"}))
+    p.set("MS", 8e5).set("AEX", 1.3e-11)
+    m0 = random_unit_vectors(515, p.shape)
+    mag = make_magnet(p, [m0])
+    assert mag.get_shape()["ty"] == 8
+    Bg, _ = gpu_eval(mag, p)
+    mag.close()
+    nx, ny, nz = p.shape
+    m = m0.astype(np.float64)
+    noct = demag.tensor_octant(p.shape, p.cell)
+    P = fields.cell_params(p)
+    local = sum(fields.effective_fields(
+        Problem(p.shape, p.cell, 1, frozenset({"EXCH"}), p.regions, p.scal, p.vec, p.glob), [m], P=P))
+    picks = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (1024, 3, 8), (513, 76, 15), (700, 151, 0), (2, 100, 7)]
+    cells = [x + nx * (y + ny * z) for x, y, z in picks]
+    Bd = demag.demag_direct(p.shape, p.cell, P["MS"][0] * m, noct=noct, cells=cells)
+    bar = 1e-5 * MU0 * 8e5
+    for (x, y, z), bd in zip(picks, Bd.T):
+        ref = bd + local[:, z, y, x]
+        assert np.abs(Bg[0][:, z, y, x] - ref).max() <= bar, ((x, y, z), Bg[0][:, z, y, x], ref)
