@@ -246,7 +246,7 @@ int mmp_get_shape(mmp_ctx* ctx, mmp_shape* out);
  * Runge-Kutta stage is dropped; results agree to FP32 rounding. */
 int mmp_set_shape(mmp_ctx* ctx, const mmp_shape* shape);
 
-#define MMP_TUNE_BATCH 1   /* only shapes a batch runs (R = 1, stage_kernel = 0) */
+#define MMP_TUNE_BATCH 1   /* only shapes a batch runs (R = 1, stage_kernel = 0), 8-row tiles */
 #define MMP_TUNE_FORCE 2   /* time again even if this geometry was tuned before */
 /* Time every valid shape on the context's current state (a few evaluations
  * of passes A, B and C each, CUDA events on the context's stream), set the

@@ -1,14 +1,17 @@
 // batch.cu -- many independent contexts advanced in lock step (host
 // driver; kernels in batch_a.cu, batch_b.cu, batch_c.cu).
 //
-// Every pass of every Dormand-Prince stage is ONE launch over a work list of
+// Every pass of every Dormand-Prince stage runs over a work list of
 // (member, tile) items of all active members: pass A (stage assembly +
-// forward x FFT) over their y tiles, pass B over their kx planes (one
-// launch per z-extent group, since the z transform is specialised per nz),
-// pass C (inverse x FFT + field + torque + error) over their tiles.  One
-// block per item; each list is sorted by decreasing work, so uneven members
-// share the GPU without a tail per member.  Stream order makes pass B wait
-// for pass A and pass C for pass B.
+// forward x FFT) over their y tiles, pass B over their kx planes, pass C
+// (inverse x FFT + field + torque + error) over their tiles.  One block per
+// item.  A pass is one launch per (z-extent group for pass B, whose z
+// transform is specialised per nz; block-size class: each member's own block
+// size rounded up to 128, 256 or 512), and these launches run concurrently
+// on side streams, so small items run in small blocks several to an SM.
+// Each list is sorted by decreasing work, so uneven members share the GPU
+// without a tail per member.  Stream order makes pass B wait for pass A and
+// pass C for pass B.
 // A fixed-step lock step (6 stages and the accept) is one CUDA graph,
 // replayed.
 //
@@ -25,6 +28,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "batch.h"
@@ -59,13 +64,12 @@ struct Member {
 };
 
 // Dynamic shared memory of a member's items in each pass.
-size_t smem_a(const Grid& g) { return passa_inv_offset(g.Px, g.ty) + (size_t)g.ty * g.nx * sizeof(float); }
+size_t smem_a(const Grid& g) { return passa_inv_offset(g.Px, g.ty, g.xb) + (size_t)g.ty * g.nx * sizeof(float); }
 size_t smem_b(const Grid& g) { return passb_smem(g.ny, g.nz, g.Py, g.kzn, 1, false).total; }
 size_t smem_c(const Grid& g) { return smem_field(g, true); }
 
 // z-extent group of pass B (the specialised z transforms).
 int nz_group(int nz) { return (nz == 1 || nz == 2 || nz == 4 || nz == 8) ? nz : 0; }
-constexpr int kGroups[5] = {1, 2, 4, 8, 0};
 
 double item_cost(const Grid& g, int pass) {
   auto lg = [](double v) { return v > 1 ? log2(v) : 1.0; };
@@ -73,13 +77,22 @@ double item_cost(const Grid& g, int pass) {
   return (double)g.ty * g.Px * lg(g.Px) + (pass == 2 ? 40.0 * g.ty * g.nx : 0.0);
 }
 
-// Launches of one stage: 0 = pass A, 1..5 = pass B per group, 6 = pass C.
-constexpr int kLaunches = 7;
+// Block size class of an item: the member's own block size for the pass
+// (launch_threads), rounded up to 128, 256 or 512 threads, so small items
+// run in small blocks and several share an SM.
+int thread_class(int t) { return t <= 128 ? 128 : (t <= 256 ? 256 : 512); }
+
+// One launch of a stage: pass kind (0 = A, 1 = B, 2 = C), z group of pass B,
+// block size, and its slice of the item array.
+struct Launch {
+  int kind, group, threads;
+  int off, cnt;
+  size_t smem;
+};
 
 struct ListSet {
   std::vector<int> members;     // member indices; descriptor k is members[k]
-  int off[kLaunches] = {}, cnt[kLaunches] = {};
-  size_t smem[kLaunches] = {};
+  std::vector<Launch> launches; // grouped by kind (A, then B, then C)
   int total = 0;
 };
 
@@ -100,6 +113,9 @@ struct mmp_batch {
   size_t cap_hred = 0;
   std::vector<BatchInst> h_inst;
   ListSet list;
+  std::vector<cudaStream_t> aux;   // side streams: the launches of one pass run concurrently
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
   bool list_valid = false;
   int sms = 0;
   // fixed-step graph of one lock step over the current list
@@ -155,7 +171,7 @@ bool eligible(const mmp_ctx* c, const char** why) {
   }
   if (c->R != 1 || c->ks != 0) { *why = "batch members use the shape R = 1, stage_kernel = 0"; return false; }
   const Grid& g = c->g;
-  if ((long long)(g.ty / 2) * g.Px > (long long)fft_cap(c->plan_x) * kBatchThreads) {
+  if ((long long)g.xb * (g.ty / 2) * g.Px > (long long)fft_cap(c->plan_x) * kBatchThreads) {
     *why = "member tiles exceed the FFT capacity of one batched block";
     return false;
   }
@@ -202,34 +218,44 @@ BatchInst make_inst(const Member& m, unsigned* red, double h, int relax) {
   return I;
 }
 
-// Work lists over `mem` (member indices): pass-A tiles, pass-B planes per
-// z group, pass-C tiles, each longest first; uploaded to d_items.
+// Work lists over `mem` (member indices): per pass kind, z group (pass B)
+// and block-size class, one launch over its items sorted longest first;
+// uploaded to d_items.
 int build_list(mmp_batch* b, const std::vector<int>& mem) {
   ListSet L;
   L.members = mem;
-  std::vector<std::pair<double, BatchItem>> sec[kLaunches];
+  std::map<std::tuple<int, int, int>, std::vector<std::pair<double, BatchItem>>> sec;
+  std::map<std::tuple<int, int, int>, size_t> smem;
   for (int k = 0; k < (int)mem.size(); ++k) {
-    const Grid& g = b->members[mem[k]].ctx->g;
+    const mmp_ctx* c = b->members[mem[k]].ctx;
+    const Grid& g = c->g;
     const int tiles = (g.ny + g.ty - 1) / g.ty;
-    int gi = 0;
-    while (kGroups[gi] != nz_group(g.nz)) ++gi;
-    L.smem[0] = std::max(L.smem[0], smem_a(g));
-    L.smem[1 + gi] = std::max(L.smem[1 + gi], smem_b(g));
-    L.smem[6] = std::max(L.smem[6], smem_c(g));
+    const auto ka = std::make_tuple(0, 0, thread_class(c->thrA));
+    const auto kb = std::make_tuple(1, nz_group(g.nz), thread_class(c->thrB));
+    const auto kc = std::make_tuple(2, 0, thread_class(c->thrC));
+    smem[ka] = std::max(smem[ka], smem_a(g));
+    smem[kb] = std::max(smem[kb], smem_b(g));
+    smem[kc] = std::max(smem[kc], smem_c(g));
     for (int z = 0; z < g.nz; ++z)
       for (int t = 0; t < tiles; ++t) {
-        sec[0].push_back({item_cost(g, 0), BatchItem{k, t, z}});
-        sec[6].push_back({item_cost(g, 2), BatchItem{k, t, z}});
+        sec[ka].push_back({item_cost(g, 0), BatchItem{k, t, z}});
+        sec[kc].push_back({item_cost(g, 2), BatchItem{k, t, z}});
       }
-    for (int kx = 0; kx < g.kxn; ++kx) sec[1 + gi].push_back({item_cost(g, 1), BatchItem{k, kx, 0}});
+    for (int kx = 0; kx < g.kxn; ++kx) sec[kb].push_back({item_cost(g, 1), BatchItem{k, kx, 0}});
   }
   std::vector<BatchItem> items;
-  for (int l = 0; l < kLaunches; ++l) {
-    auto& s = sec[l];
-    std::stable_sort(s.begin(), s.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-    L.off[l] = (int)items.size();
-    L.cnt[l] = (int)s.size();
-    for (auto& e : s) items.push_back(e.second);
+  for (auto& kv : sec) {   // std::map order: kind, then group, then block size
+    auto& v = kv.second;
+    std::stable_sort(v.begin(), v.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    Launch l;
+    l.kind = std::get<0>(kv.first);
+    l.group = std::get<1>(kv.first);
+    l.threads = std::get<2>(kv.first);
+    l.off = (int)items.size();
+    l.cnt = (int)v.size();
+    l.smem = smem[kv.first];
+    for (auto& e : v) items.push_back(e.second);
+    L.launches.push_back(l);
   }
   L.total = (int)items.size();
   BTRY(grow_buf(b->d_items, b->cap_items, items.size()));
@@ -237,13 +263,29 @@ int build_list(mmp_batch* b, const std::vector<int>& mem) {
   BCK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
                       b->stream),
       "batch: upload work list");
+  // side streams and events for the widest pass
+  size_t widest = 0;
+  for (int kind = 0; kind < 3; ++kind) {
+    size_t n = 0;
+    for (const Launch& l : L.launches) n += l.kind == kind;
+    widest = std::max(widest, n);
+  }
+  if (!b->fork) BCK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch: event");
+  while (b->aux.size() + 1 < widest) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    BCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "batch: side stream");
+    BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch: event");
+    b->aux.push_back(st);
+    b->join.push_back(ev);
+  }
   b->list = L;
   b->list_valid = true;
   b->graph_valid = false;
   return MMP_OK;
 }
 
-// Events around one launch of pass kind k (0 = A, 1 = B, 2 = C) when tracing.
+// Events around the launches of pass kind k (0 = A, 1 = B, 2 = C) when tracing.
 struct BTraced {
   mmp_batch* b;
   cudaEvent_t stop = nullptr;
@@ -265,29 +307,34 @@ struct BTraced {
   }
 };
 
-// Enqueue stage `stage` of the current list: pass A, pass B per z group,
-// pass C.
+cudaError_t launch_one(mmp_batch* b, const Launch& l, int stage, cudaStream_t s) {
+  const BatchItem* it = b->d_items + l.off;
+  if (l.kind == 0) return launch_batch_passA(b->d_inst, it, l.cnt, stage, l.threads, l.smem, s);
+  if (l.kind == 1) return launch_batch_passB(l.group, b->d_inst, it, l.cnt, l.threads, l.smem, s);
+  return launch_batch_field(b->d_inst, it, l.cnt, stage, l.threads, l.smem, s);
+}
+
+// Enqueue stage `stage` of the current list: the launches of pass A, then
+// of pass B, then of pass C; the launches of one pass run concurrently on
+// side streams forked from and joined back into the batch stream.
 int launch_stage(mmp_batch* b, int stage) {
-  const ListSet& L = b->list;
-  if (L.cnt[0]) {
-    BTraced t(b, 0);
-    BCK(launch_batch_passA(b->d_inst, b->d_items + L.off[0], L.cnt[0], stage, L.smem[0], b->stream),
-        "batch: pass A");
-    b->launches++;
-  }
-  for (int gi = 0; gi < 5; ++gi) {
-    const int l = 1 + gi;
-    if (!L.cnt[l]) continue;
-    BTraced t(b, 1);
-    BCK(launch_batch_passB(kGroups[gi], b->d_inst, b->d_items + L.off[l], L.cnt[l], L.smem[l], b->stream),
-        "batch: pass B");
-    b->launches++;
-  }
-  if (L.cnt[6]) {
-    BTraced t(b, 2);
-    BCK(launch_batch_field(b->d_inst, b->d_items + L.off[6], L.cnt[6], stage, L.smem[6], b->stream),
-        "batch: pass C");
-    b->launches++;
+  for (int kind = 0; kind < 3; ++kind) {
+    std::vector<const Launch*> ls;
+    for (const Launch& l : b->list.launches)
+      if (l.kind == kind) ls.push_back(&l);
+    if (ls.empty()) continue;
+    BTraced t(b, kind);
+    if (ls.size() > 1) BCK(cudaEventRecord(b->fork, b->stream), "batch: fork");
+    for (size_t i = 0; i < ls.size(); ++i) {
+      cudaStream_t s = i == 0 ? b->stream : b->aux[i - 1];
+      if (i > 0) BCK(cudaStreamWaitEvent(s, b->fork, 0), "batch: fork wait");
+      BCK(launch_one(b, *ls[i], stage, s), "batch: pass launch");
+      b->launches++;
+      if (i > 0) {
+        BCK(cudaEventRecord(b->join[i - 1], s), "batch: join");
+        BCK(cudaStreamWaitEvent(b->stream, b->join[i - 1], 0), "batch: join wait");
+      }
+    }
   }
   return MMP_OK;
 }
@@ -359,6 +406,9 @@ int mmp_batch_destroy(mmp_batch* b) {
   cudaStreamSynchronize(b->stream);
   settle(b);
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (cudaStream_t st : b->aux) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
   for (auto& v : b->prof_events)
     for (auto& pr : v) {
       cudaEventDestroy(pr.first);

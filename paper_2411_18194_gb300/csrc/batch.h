@@ -38,12 +38,14 @@ constexpr int kBatchThreads = 512;
 // `stage`: 0 evaluates k1 at y (no assembly); 1..6 assemble stage i and
 // evaluate k_{i+1}; stage 6 also forms the error estimate and torque
 // maximum.
-cudaError_t launch_batch_passA(const BatchInst* insts, const BatchItem* items, int nitems, int stage, size_t smem,
-                               cudaStream_t s);
-cudaError_t launch_batch_passB(int nz_group, const BatchInst* insts, const BatchItem* items, int nitems,
+// `threads` <= kBatchThreads: the block size of the launch (items are
+// grouped by the block size their member needs).
+cudaError_t launch_batch_passA(const BatchInst* insts, const BatchItem* items, int nitems, int stage, int threads,
                                size_t smem, cudaStream_t s);
-cudaError_t launch_batch_field(const BatchInst* insts, const BatchItem* items, int nitems, int stage, size_t smem,
-                               cudaStream_t s);
+cudaError_t launch_batch_passB(int nz_group, const BatchInst* insts, const BatchItem* items, int nitems,
+                               int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_field(const BatchInst* insts, const BatchItem* items, int nitems, int stage, int threads,
+                               size_t smem, cudaStream_t s);
 cudaError_t launch_batch_accept(BatchInst* insts, int n, cudaStream_t s);
 
 // Stage and field arguments of item descriptor `I` at stage `stage`

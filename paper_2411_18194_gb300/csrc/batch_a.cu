@@ -18,15 +18,15 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_passA(const BatchInst* 
   passA_tile<1, ASSEMBLE>(sraw, si.g, sa, si.d, si.co, w.b, w.a * si.g.ty);
 }
 
-cudaError_t launch_batch_passA(const BatchInst* insts, const BatchItem* items, int nitems, int stage, size_t smem,
-                               cudaStream_t s) {
+cudaError_t launch_batch_passA(const BatchInst* insts, const BatchItem* items, int nitems, int stage, int threads,
+                               size_t smem, cudaStream_t s) {
   cudaError_t e;
   if (stage == 0) {
     if ((e = set_smem(k_batch_passA<false>, smem)) != cudaSuccess) return e;
-    k_batch_passA<false><<<nitems, kBatchThreads, smem, s>>>(insts, items, stage);
+    k_batch_passA<false><<<nitems, threads, smem, s>>>(insts, items, stage);
   } else {
     if ((e = set_smem(k_batch_passA<true>, smem)) != cudaSuccess) return e;
-    k_batch_passA<true><<<nitems, kBatchThreads, smem, s>>>(insts, items, stage);
+    k_batch_passA<true><<<nitems, threads, smem, s>>>(insts, items, stage);
   }
   return cudaGetLastError();
 }

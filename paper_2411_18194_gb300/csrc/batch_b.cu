@@ -17,22 +17,22 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_passB(const BatchInst* 
 }
 
 template <int NZ>
-static cudaError_t launch_b(const BatchInst* insts, const BatchItem* items, int nitems, size_t smem,
+static cudaError_t launch_b(const BatchInst* insts, const BatchItem* items, int nitems, int threads, size_t smem,
                             cudaStream_t s) {
   cudaError_t e = set_smem(k_batch_passB<NZ>, smem);
   if (e != cudaSuccess) return e;
-  k_batch_passB<NZ><<<nitems, kBatchThreads, smem, s>>>(insts, items);
+  k_batch_passB<NZ><<<nitems, threads, smem, s>>>(insts, items);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_passB(int nz_group, const BatchInst* insts, const BatchItem* items, int nitems,
-                               size_t smem, cudaStream_t s) {
+                               int threads, size_t smem, cudaStream_t s) {
   switch (nz_group) {
-    case 1: return launch_b<1>(insts, items, nitems, smem, s);
-    case 2: return launch_b<2>(insts, items, nitems, smem, s);
-    case 4: return launch_b<4>(insts, items, nitems, smem, s);
-    case 8: return launch_b<8>(insts, items, nitems, smem, s);
-    default: return launch_b<0>(insts, items, nitems, smem, s);
+    case 1: return launch_b<1>(insts, items, nitems, threads, smem, s);
+    case 2: return launch_b<2>(insts, items, nitems, threads, smem, s);
+    case 4: return launch_b<4>(insts, items, nitems, threads, smem, s);
+    case 8: return launch_b<8>(insts, items, nitems, threads, smem, s);
+    default: return launch_b<0>(insts, items, nitems, threads, smem, s);
   }
 }
 

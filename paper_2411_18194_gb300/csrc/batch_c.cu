@@ -25,11 +25,11 @@ __global__ void k_batch_accept(BatchInst* insts, int n) {
   if (i < n) insts[i].par ^= 1;
 }
 
-cudaError_t launch_batch_field(const BatchInst* insts, const BatchItem* items, int nitems, int stage, size_t smem,
-                               cudaStream_t s) {
+cudaError_t launch_batch_field(const BatchInst* insts, const BatchItem* items, int nitems, int stage, int threads,
+                               size_t smem, cudaStream_t s) {
   cudaError_t e = set_smem(k_batch_field, smem);
   if (e != cudaSuccess) return e;
-  k_batch_field<<<nitems, kBatchThreads, smem, s>>>(insts, items, stage);
+  k_batch_field<<<nitems, threads, smem, s>>>(insts, items, stage);
   return cudaGetLastError();
 }
 

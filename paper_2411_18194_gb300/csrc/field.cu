@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(512) k_field(Grid g, DemagArgs d, Coefs co, Fi
 size_t smem_field(const Grid& g, bool demag) {
   if (!demag) return 0;
   return (size_t)((3 * g.ty * g.nx + 3) & ~3) * sizeof(float) +
-         ((size_t)(g.ty >> 1) * fft_pitch(g.Px) + g.Px) * sizeof(float2);
+         ((size_t)g.xb * (g.ty >> 1) * fft_pitch(g.Px) + g.Px) * sizeof(float2);
 }
 
 cudaError_t launch_field(const Grid& g, const DemagArgs& d, const Coefs& c, const FieldArgs& f, int nsub,

@@ -173,28 +173,33 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
   return o;
 }
 
-// One component of the inverse x transform of pass C: Hermitian-extended
-// row pairs from T, inverse FFT, the x < nx outputs into bd[c][row][x].
-__device__ __forceinline__ void inverse_x_component(int c, float2* fbuf, const float2* tw, float* bd,
-                                                    const Grid& g, const DemagArgs& d, int z, int y0) {
+// Components c0 .. c0 + nc - 1 of the inverse x transform of pass C:
+// Hermitian-extended row pairs from T (transform (c - c0) np + p), one
+// inverse block_fft, the x < nx outputs into bd[c][row][x].
+__device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbuf, const float2* tw, float* bd,
+                                                     const Grid& g, const DemagArgs& d, int z, int y0) {
+  if (nc == 0) return;
   const int nx = g.nx, ny = g.ny, Px = g.Px;
   const int pitch = fft_pitch(Px);
-  for (int e = threadIdx.x; e < (g.ty >> 1) * Px; e += blockDim.x) {
-    int k = e / (g.ty >> 1), p = e - k * (g.ty >> 1);
-    int kk = k <= Px / 2 ? k : Px - k;
-    int ya = y0 + 2 * p, yb = ya + 1;
-    const float2* Tc = d.T + (((long long)kk * 3 + c) * g.nz + z) * ny;
+  const int np = g.ty >> 1;
+  for (int e = threadIdx.x; e < nc * np * Px; e += blockDim.x) {
+    const int cc = e / (np * Px), r = e - cc * (np * Px);
+    const int k = r / np, p = r - k * np;
+    const int kk = k <= Px / 2 ? k : Px - k;
+    const int ya = y0 + 2 * p, yb = ya + 1;
+    const float2* Tc = d.T + (((long long)kk * 3 + c0 + cc) * g.nz + z) * ny;
     float2 xa = ya < ny ? __ldcg(Tc + ya) : make_float2(0.0f, 0.0f);
     float2 xb = yb < ny ? __ldcg(Tc + yb) : make_float2(0.0f, 0.0f);
     if (k > Px / 2) { xa.y = -xa.y; xb.y = -xb.y; }
-    fbuf[fidx(p, k, pitch)] = make_float2(xa.x - xb.y, xa.y + xb.x);
+    fbuf[fidx(cc * np + p, k, pitch)] = make_float2(xa.x - xb.y, xa.y + xb.x);
   }
   __syncthreads();
-  block_fft<true>(fbuf, d.plan_x, (g.ty >> 1), tw);
-  for (int e = threadIdx.x; e < g.ty * nx; e += blockDim.x) {
-    int row = e / nx, x = e - row * nx;
-    float2 v = fbuf[fidx(row >> 1, x, pitch)];
-    bd[(c * g.ty + row) * nx + x] = (row & 1) ? v.y : v.x;
+  block_fft<true>(fbuf, d.plan_x, nc * np, tw);
+  for (int e = threadIdx.x; e < nc * g.ty * nx; e += blockDim.x) {
+    const int cc = e / (g.ty * nx), r = e - cc * (g.ty * nx);
+    const int row = r / nx, x = r - row * nx;
+    float2 v = fbuf[fidx(cc * np + (row >> 1), x, pitch)];
+    bd[((c0 + cc) * g.ty + row) * nx + x] = (row & 1) ? v.y : v.x;
   }
   __syncthreads();
 }
@@ -208,11 +213,13 @@ __device__ __forceinline__ void field_tile(float* smem, const Grid& g, const Dem
   float* bd = smem;                                                     // [3][TY][nx]
   float2* fbuf = reinterpret_cast<float2*>(smem + ((3 * g.ty * nx + 3) & ~3));   // [NP][Px]
   if (DEMAG) {
-    float2* tw = fbuf + (g.ty >> 1) * fft_pitch(Px);
+    float2* tw = fbuf + g.xb * (g.ty >> 1) * fft_pitch(Px);
     for (int i = threadIdx.x; i < Px; i += blockDim.x) tw[i] = __ldg(d.tw_x + i);
-    inverse_x_component(0, fbuf, tw, bd, g, d, z, y0);
-    inverse_x_component(1, fbuf, tw, bd, g, d, z, y0);
-    inverse_x_component(2, fbuf, tw, bd, g, d, z, y0);
+    // straight-line calls, as in pass A; with xb = 3 the first does all three
+    const int rest = g.xb == 3 ? 0 : 1;
+    inverse_x_components(0, g.xb == 3 ? 3 : 1, fbuf, tw, bd, g, d, z, y0);
+    inverse_x_components(1, rest, fbuf, tw, bd, g, d, z, y0);
+    inverse_x_components(2, rest, fbuf, tw, bd, g, d, z, y0);
   }
   float emax = 0.0f, tmax = 0.0f;
   const long long n = g.n;

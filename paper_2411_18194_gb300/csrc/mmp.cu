@@ -375,6 +375,13 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
   TRY(upload_table(ctx, ctx->d_tw_x, pass_twiddles(ctx->plan_x)));
   TRY(upload_table(ctx, ctx->d_tw_ly, pass_twiddles(ctx->plan_ly)));
   g.ty = s.ty;
+  // all three components in one x-FFT call when a 512-thread block holds
+  // them and the shared memory of passes A and C fits
+  g.xb = 3;
+  if ((long long)3 * (g.ty / 2) * g.Px > (long long)fft_cap(ctx->plan_x) * 512 ||
+      smem_passA(g) + (size_t)ctx->nsub * g.ty * g.nx * sizeof(float) > 227 * 1024 ||
+      smem_field(g, true) > 227 * 1024)
+    g.xb = 1;
   ctx->R = s.R;
   ctx->ks = s.stage_kernel != 0;
   ctx->radix_x = s.radix_x;
@@ -688,6 +695,7 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
   g.kxn = g.Px / 2 + 1; g.kyn = g.Py / 2 + 1; g.kzn = g.Pz / 2 + 1;
   g.krow = (6 * g.kzn + 3) & ~3;
   g.ty = pick_tile_rows(g.ny, g.nz);
+  g.xb = 1;
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (float)ctx->cell[a];
     g.ih[a] = (float)(1.0 / ctx->cell[a]);
@@ -1058,8 +1066,10 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
   // passes A and C: tile rows and x plan (pass B fixed)
   double best_ac = 1e300;
   mmp_shape base = best;
+  // (a batch gets its parallelism from its members: the largest tiles, fewest items)
   for (int ty : {2, 4, 8})
     for (int rx = 0; rx < 2; ++rx) {
+      if (batch && ty != 8) continue;
       mmp_shape s = base;
       s.ty = ty;
       s.radix_x = rx;

@@ -34,9 +34,9 @@ __global__ void __launch_bounds__(512) k_passA(Grid g, StageArgs a, DemagArgs d,
   passA_tile<NSUB, ASSEMBLE>(sraw, g, a, d, co, blockIdx.y, blockIdx.x * g.ty);
 }
 
-size_t smem_passA(const Grid& g) { return passa_inv_offset(g.Px, g.ty); }
+size_t smem_passA(const Grid& g) { return passa_inv_offset(g.Px, g.ty, g.xb); }
 static size_t smem_passA_launch(const Grid& g, const StageArgs& a) {
-  return passa_inv_offset(g.Px, g.ty) + (a.normalize ? (size_t)a.nsub * g.ty * g.nx * sizeof(float) : 0);
+  return passa_inv_offset(g.Px, g.ty, g.xb) + (a.normalize ? (size_t)a.nsub * g.ty * g.nx * sizeof(float) : 0);
 }
 
 cudaError_t launch_assemble(const Grid& g, const StageArgs& a, cudaStream_t s) {

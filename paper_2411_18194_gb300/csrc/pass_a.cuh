@@ -9,14 +9,14 @@
 namespace mmp {
 
 // ------------------------------------------------------------- pass A ----
-// Shared memory: the row-pair FFT buffer (padded layout), the length-Px
-// twiddles, and for the renormalised stage 1/|m_i| of every tile cell and
-// sublattice.
-__host__ __device__ __forceinline__ size_t passa_twiddle_offset(int Px, int ty) {
-  return (size_t)(ty >> 1) * fft_pitch(Px) * sizeof(float2);
+// Shared memory: the row-pair FFT buffer (padded layout) of xb components,
+// the length-Px twiddles, and for the renormalised stage 1/|m_i| of every
+// tile cell and sublattice.
+__host__ __device__ __forceinline__ size_t passa_twiddle_offset(int Px, int ty, int xb) {
+  return (size_t)xb * (ty >> 1) * fft_pitch(Px) * sizeof(float2);
 }
-__host__ __device__ __forceinline__ size_t passa_inv_offset(int Px, int ty) {
-  return passa_twiddle_offset(Px, ty) + (size_t)Px * sizeof(float2);
+__host__ __device__ __forceinline__ size_t passa_inv_offset(int Px, int ty, int xb) {
+  return passa_twiddle_offset(Px, ty, xb) + (size_t)Px * sizeof(float2);
 }
 
 // Stage value of component c of part p at a cell: assembled from y and the
@@ -32,20 +32,24 @@ __device__ __forceinline__ float stage_value(const StageArgs& a, long long n, in
   return acc;
 }
 
-// One component of pass A: the stage values of component c are assembled
+// Components c0 .. c0 + nc - 1 of pass A: the stage values are assembled
 // straight into the FFT input (and written to the stage state once), M_c is
-// packed in row pairs, transformed, and the unpacked half spectra are
-// written to T.  Called three times in straight-line code (a loop over c
-// made the compiler keep the FFT pass registers in local memory).
+// packed in row pairs (transform (c - c0) np + p), all nc np transforms are
+// done in one block_fft, and the unpacked half spectra are written to T.
+// nc = 3 (g.xb) when the block holds all three components, else one call
+// per component.
 template <int NSUB, bool ASSEMBLE>
-__device__ __forceinline__ void passA_component(int c, float2* fbuf, const float2* tw, const float* inv,
-                                                const Grid& g, const StageArgs& a, const DemagArgs& d,
-                                                const Coefs& co, int z, int y0) {
+__device__ __forceinline__ void passA_components(int c0, int nc, float2* fbuf, const float2* tw, const float* inv,
+                                                 const Grid& g, const StageArgs& a, const DemagArgs& d,
+                                                 const Coefs& co, int z, int y0) {
+  if (nc == 0) return;
   const int nx = g.nx, ny = g.ny, Px = g.Px;
   const int pitch = fft_pitch(Px);
+  const int np = g.ty >> 1;
   const long long n = g.n;
-  for (int e = threadIdx.x; e < (g.ty >> 1) * Px; e += blockDim.x) {
-    int p = e / Px, x = e - p * Px;
+  for (int e = threadIdx.x; e < nc * np * Px; e += blockDim.x) {
+    const int t = e / Px, x = e - t * Px;
+    const int cc = t / np, p = t - cc * np, c = c0 + cc;
     float v2[2] = {0.0f, 0.0f};
     if (x < nx) {
 #pragma unroll
@@ -65,20 +69,21 @@ __device__ __forceinline__ void passA_component(int c, float2* fbuf, const float
         }
       }
     }
-    fbuf[fidx(p, x, pitch)] = make_float2(v2[0], v2[1]);
+    fbuf[fidx(t, x, pitch)] = make_float2(v2[0], v2[1]);
   }
   __syncthreads();
-  block_fft<false>(fbuf, d.plan_x, (g.ty >> 1), tw);
-  for (int e = threadIdx.x; e < g.kxn * g.ty; e += blockDim.x) {
-    int k = e / g.ty, row = e - k * g.ty, y = y0 + row;
+  block_fft<false>(fbuf, d.plan_x, nc * np, tw);
+  for (int e = threadIdx.x; e < nc * g.kxn * g.ty; e += blockDim.x) {
+    const int cc = e / (g.kxn * g.ty), r = e - cc * (g.kxn * g.ty);
+    const int k = r / g.ty, row = r - k * g.ty, y = y0 + row;
     if (y >= ny) continue;
-    int p = row >> 1;
-    float2 Z = fbuf[fidx(p, k, pitch)];
-    float2 Zm = fbuf[fidx(p, k == 0 ? 0 : Px - k, pitch)];
+    const int t = cc * np + (row >> 1);
+    float2 Z = fbuf[fidx(t, k, pitch)];
+    float2 Zm = fbuf[fidx(t, k == 0 ? 0 : Px - k, pitch)];
     float2 X;
     if ((row & 1) == 0) X = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
     else X = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
-    d.T[(((long long)k * 3 + c) * g.nz + z) * ny + y] = X;
+    d.T[(((long long)k * 3 + c0 + cc) * g.nz + z) * ny + y] = X;
   }
   __syncthreads();
 }
@@ -90,8 +95,8 @@ __device__ __forceinline__ void passA_tile(unsigned char* sraw, const Grid& g, c
                                            const DemagArgs& d, const Coefs& co, int z, int y0) {
   const int Px = g.Px, nx = g.nx, ny = g.ny;
   float2* fbuf = reinterpret_cast<float2*>(sraw);
-  float2* tw = reinterpret_cast<float2*>(sraw + passa_twiddle_offset(Px, g.ty));
-  float* inv = reinterpret_cast<float*>(sraw + passa_inv_offset(Px, g.ty));
+  float2* tw = reinterpret_cast<float2*>(sraw + passa_twiddle_offset(Px, g.ty, g.xb));
+  float* inv = reinterpret_cast<float*>(sraw + passa_inv_offset(Px, g.ty, g.xb));
   const long long n = g.n;
   for (int i = threadIdx.x; i < Px; i += blockDim.x) tw[i] = __ldg(d.tw_x + i);
   if (ASSEMBLE && (a.normalize || a.nparts > a.nsub)) {
@@ -115,9 +120,12 @@ __device__ __forceinline__ void passA_tile(unsigned char* sraw, const Grid& g, c
     }
   }
   __syncthreads();
-  passA_component<NSUB, ASSEMBLE>(0, fbuf, tw, inv, g, a, d, co, z, y0);
-  passA_component<NSUB, ASSEMBLE>(1, fbuf, tw, inv, g, a, d, co, z, y0);
-  passA_component<NSUB, ASSEMBLE>(2, fbuf, tw, inv, g, a, d, co, z, y0);
+  // straight-line calls (a loop around the FFT body makes the compiler cut
+  // the registers and spill); with xb = 3 the first call does all three
+  const int rest = g.xb == 3 ? 0 : 1;
+  passA_components<NSUB, ASSEMBLE>(0, g.xb == 3 ? 3 : 1, fbuf, tw, inv, g, a, d, co, z, y0);
+  passA_components<NSUB, ASSEMBLE>(1, rest, fbuf, tw, inv, g, a, d, co, z, y0);
+  passA_components<NSUB, ASSEMBLE>(2, rest, fbuf, tw, inv, g, a, d, co, z, y0);
 }
 
 }  // namespace mmp

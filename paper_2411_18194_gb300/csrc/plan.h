@@ -132,7 +132,7 @@ inline void launch_threads(const Grid& g, int R, int* thrA, int* thrB, int* thrC
   auto r32 = [](long long v) { return (int)((v + 31) / 32 * 32); };
   auto need = [](long long el, int cap) { return (el + cap - 1) / cap; };
   const int np = g.ty >> 1;
-  const long long fx = need((long long)np * g.Px, fft_cap(g.Px));
+  const long long fx = need((long long)g.xb * np * g.Px, fft_cap(g.Px));
   *thrA = std::min(512, std::max(128, r32(fx)));
   const int Ly = g.Py / R;
   const long long elB = (long long)3 * g.nz * Ly;
