@@ -248,12 +248,17 @@ int mmp_set_shape(mmp_ctx* ctx, const mmp_shape* shape);
 
 #define MMP_TUNE_BATCH 1   /* only shapes a batch runs (R = 1, stage_kernel = 0), 8-row tiles */
 #define MMP_TUNE_FORCE 2   /* time again even if this geometry was tuned before */
-/* Time every valid shape on the context's current state (a few evaluations
- * of passes A, B and C each, CUDA events on the context's stream), set the
- * fastest and return it (chosen, may be NULL) with its time per field
- * evaluation in ms (eval_ms, may be NULL).  Results are cached per
- * (grid, sublattices, flags) in the process; a cached geometry is set
- * without timing unless MMP_TUNE_FORCE.  Synchronises the stream. */
+/* Time the valid shapes on the context's current state and keep the
+ * fastest: after a warm-up of ~100 ms of evaluations (loaded clocks), the
+ * candidates of passes A+C (tile rows, x plan) and of pass B (R, staging,
+ * y plan) are timed separately in two interleaved rounds (CUDA events per
+ * pass on the context's stream, the better round counts); the combination
+ * replaces the starting shape only if a longer interleaved measurement
+ * finds it > 2 % faster per evaluation.  Returns the shape (chosen, may be
+ * NULL) and its time per field evaluation in ms (eval_ms, may be NULL).
+ * Results are cached per (grid, sublattices, flags) in the process; a
+ * cached geometry is set without timing unless MMP_TUNE_FORCE.
+ * Synchronises the stream. */
 int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms);
 
 /* ---------------------------------------------------------------------

@@ -3,8 +3,14 @@
 Each CUDA translation unit is compiled in its own nvcc process (in
 parallel), then linked into paper_2411_18194_gb300/_lib/libmmp.so with the
 CUDA runtime linked statically.
+
+ptxas reports every kernel's registers and spills; the build fails if a
+kernel spills more than SPILL_LIMIT bytes.  (A loop around an inlined FFT
+body once made the compiler cut a kernel to 32 registers and spill
+kilobytes per thread, several times slower, with no other symptom.)
 """
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -16,6 +22,7 @@ OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libmmp.so")
 SOURCES = ["mmp.cu", "pass_a.cu", "pass_b.cu", "field.cu", "elastic.cu", "tensor.cu", "noalloc.cu", "batch.cu", "batch_a.cu", "batch_b.cu", "batch_c.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+SPILL_LIMIT = 1024   # bytes of spill stores per thread
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + SRC]
 
@@ -27,6 +34,19 @@ def nvcc():
     return path
 
 
+def check_spills(ptxas_out):
+    """Kernels whose spill stores exceed SPILL_LIMIT in a ptxas -v log."""
+    bad, name = [], None
+    for line in ptxas_out.splitlines():
+        m = re.search(r"Compiling entry function '([^']+)'", line)
+        if m:
+            name = m.group(1)
+        m = re.search(r"(\d+) bytes spill stores", line)
+        if m and name and int(m.group(1)) > SPILL_LIMIT:
+            bad.append("%s: %s bytes spill stores" % (name, m.group(1)))
+    return bad
+
+
 def build(verbose=False, extra=()):
     os.makedirs(OUT, exist_ok=True)
     procs = []
@@ -34,17 +54,20 @@ def build(verbose=False, extra=()):
     for src in SOURCES:
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc(), "-c", os.path.join(SRC, src), "-o", obj] + ARCH + FLAGS + list(extra)
+        cmd = [nvcc(), "-c", os.path.join(SRC, src), "-o", obj] + ARCH + FLAGS + ["-Xptxas", "-v"] + list(extra)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
-    failed = []
+    failed, spills = [], []
     for cmd, p in procs:
         out, _ = p.communicate()
         if verbose or p.returncode != 0:
             sys.stdout.write(out)
         if p.returncode != 0:
             failed.append(" ".join(cmd))
+        spills += check_spills(out)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
+    if spills:
+        raise RuntimeError("kernels spill more than %d bytes:\n" % SPILL_LIMIT + "\n".join(spills))
     tmp = LIB + ".tmp"
     link = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
@@ -55,4 +78,4 @@ def build(verbose=False, extra=()):
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+    print(build(verbose="-v" in sys.argv))

@@ -195,10 +195,13 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
     }
   }
   __syncthreads();
-  // columns per transform call: what the block holds (all of them on the
-  // per-context path; planes larger than a block are done in chunks)
-  const int cmax = max(1, (d.plan_ly.n3 ? 30 : 32) * (int)blockDim.x / Ly);
-  for (int c0 = 0; c0 < ncol; c0 += cmax) block_fft<false>(W + c0 * pitch, d.plan_ly, min(cmax, ncol - c0), twl);
+  // columns per transform call: what the block holds -- all of them on the
+  // per-context path; a larger plane (batched path) in two chunks, which the
+  // host guarantees suffice.  Two straight-line calls: a loop around the FFT
+  // body makes the compiler cut the registers and spill.
+  const int c1 = min(ncol, max(1, (d.plan_ly.n3 ? 30 : 32) * (int)blockDim.x / Ly));
+  block_fft<false>(W, d.plan_ly, c1, twl);
+  if (ncol > c1) block_fft<false>(W + c1 * pitch, d.plan_ly, ncol - c1, twl);
   if (KS) cp_async_wait_all();
   __syncthreads();
   const float* Kb = KS ? Ks : kbase;   // row of ky' = R k' + r at Kb + (KS ? k' : |ky|) krow
@@ -228,7 +231,8 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
     }
   }
   __syncthreads();
-  for (int c0 = 0; c0 < ncol; c0 += cmax) block_fft<true>(W + c0 * pitch, d.plan_ly, min(cmax, ncol - c0), twl);
+  block_fft<true>(W, d.plan_ly, c1, twl);
+  if (ncol > c1) block_fft<true>(W + c1 * pitch, d.plan_ly, ncol - c1, twl);
   // 4. recombine: out[y] = sum_q w^(-q y) h_q[y mod Ly], y < ny
   if (R == 1) {
     for (int e = threadIdx.x; e < ncol * ny; e += blockDim.x) {
