@@ -477,7 +477,10 @@ def run_gpu(args):
     m0 = torch.from_numpy(w.m0[0]).cuda()
     mag.set_solver(adaptive=w.adaptive, dt=w.dt, tol=w.tol, dt_min=1e-18, dt_max=1e-11)
     t0 = time.perf_counter()
-    shape, tuned_ms = mag.autotune()          # launch shape chosen by timing (outside the timed region)
+    if args.shape:
+        shape = mag.set_shape(**parse_shape(args.shape))
+    else:
+        shape, tuned_ms = mag.autotune()      # launch shape chosen by timing (outside the timed region)
     t_tune = time.perf_counter() - t0
 
     def barrier():
@@ -547,6 +550,28 @@ def run_gpu(args):
     _, (e2e_all,) = reduce_over_ranks([], [e2e_value], "cuda")
     nbytes = 12 * nx * ny * nz
 
+    # fixed-step single instance: the same context as the one member of a
+    # batch, whose lock steps replay from a CUDA graph (launch-bound grids)
+    graph_path = None
+    if args.workload == "c1":
+        mag.set_shape(R=1, stage_kernel=0)
+        bt = pkg.Batch(stream)
+        bt.add(mag, "steps", args.warmup + args.steps)
+        bt.advance(args.warmup)
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        bt.advance(args.steps)
+        g1.record(stream)
+        barrier()
+        gms = g0.elapsed_time(g1)
+        glaunch = bt.launches()
+        bt.close()
+        graph_path = {"value": 6 * args.steps * ncell / (gms * 1e-3) / 1e6, "unit": UNIT,
+                      "ms_per_step": gms / args.steps, "launches_total": glaunch,
+                      "what": "the same context as the only member of an mmp_batch: fixed lock steps "
+                              "replayed from a CUDA graph (shape R=1, kernel rows from L2)"}
+
     if rank == 0:
         line = {
             "metric": METRIC, "baseline_metric": BASELINE_METRIC, "value": value, "unit": UNIT,
@@ -573,11 +598,19 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk,
         }
+        if graph_path:
+            line["graph_path"] = graph_path
         print(json.dumps(line))
     mag.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def parse_shape(text):
+    """--shape ty,radix_x,radix_y,R,stage_kernel"""
+    v = [int(x) for x in text.split(",")]
+    return dict(zip(("ty", "radix_x", "radix_y", "R", "stage_kernel"), v))
 
 
 def run_profile_evals(args):
@@ -590,7 +623,10 @@ def run_profile_evals(args):
     mag = pkg.Magnet.from_problem(w.problem)
     mag.set_m(0, torch.from_numpy(w.m0[0]).cuda())
     mag.set_solver(adaptive=True, dt=w.dt, tol=w.tol)
-    mag.autotune()                       # the shape the benchmark times
+    if args.shape:
+        mag.set_shape(**parse_shape(args.shape))
+    else:
+        mag.autotune()                   # the shape the benchmark times
     for _ in range(args.profile_evals):
         mag.eval_field(0)
         mag.step(1)
@@ -610,6 +646,8 @@ def main():
                     help="c2 (default, the benchmark line); c1, c3 for the other single workloads; "
                          "c4 the batch of uneven instances; c5 the served request stream")
     ap.add_argument("--instances", type=int, default=256, help="c4: number of instances")
+    ap.add_argument("--shape", default="", help="single workloads: ty,radix_x,radix_y,R,stage_kernel "
+                                                "instead of the autotuned shape (profiling commands)")
     ap.add_argument("--requests", type=int, default=48, help="c5: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="c5: mean arrival rate (1/s)")
     ap.add_argument("--torque-tol", type=float, default=1e-2, help="c5: relax torque tolerance (T)")

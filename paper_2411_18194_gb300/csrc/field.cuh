@@ -182,22 +182,45 @@ __device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbu
   const int nx = g.nx, ny = g.ny, Px = g.Px;
   const int pitch = fft_pitch(Px);
   const int np = g.ty >> 1;
-  for (int e = threadIdx.x; e < nc * np * Px; e += blockDim.x) {
-    const int cc = e / (np * Px), r = e - cc * (np * Px);
-    const int k = r / np, p = r - k * np;
-    const int kk = k <= Px / 2 ? k : Px - k;
-    const int ya = y0 + 2 * p, yb = ya + 1;
-    const float2* Tc = d.T + (((long long)kk * 3 + c0 + cc) * g.nz + z) * ny;
-    float2 xa = ya < ny ? __ldcg(Tc + ya) : make_float2(0.0f, 0.0f);
-    float2 xb = yb < ny ? __ldcg(Tc + yb) : make_float2(0.0f, 0.0f);
-    if (k > Px / 2) { xa.y = -xa.y; xb.y = -xb.y; }
-    fbuf[fidx(cc * np + p, k, pitch)] = make_float2(xa.x - xb.y, xa.y + xb.x);
+  // groups of FU elements per thread: all loads first, then the stores
+  constexpr int FU = 4;
+  const int total = nc * np * Px;
+  // e / (np Px) by the FP32 quotient of e + 1/2, exact for e < 2^22 (its
+  // error (e / d) 2^-23 is below its 1/(2d) distance to an integer); np is
+  // a power of two
+  const float rnp = 1.0f / (float)(np * Px);
+  const int npsh = __ffs(np) - 1;
+  for (int e0 = threadIdx.x; e0 < total; e0 += FU * blockDim.x) {
+    float2 va[FU], vb[FU];
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int cc = (int)(((float)e + 0.5f) * rnp), r = e - cc * (np * Px);
+      const int k = r >> npsh, p = r & (np - 1);
+      const int kk = k <= Px / 2 ? k : Px - k;
+      const int ya = y0 + 2 * p, yb = ya + 1;
+      const float2* Tc = d.T + (((long long)kk * 3 + c0 + cc) * g.nz + z) * ny;
+      const bool ok = e < total;
+      va[u] = ok && ya < ny ? __ldcg(Tc + ya) : make_float2(0.0f, 0.0f);
+      vb[u] = ok && yb < ny ? __ldcg(Tc + yb) : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= total) continue;
+      const int cc = (int)(((float)e + 0.5f) * rnp), r = e - cc * (np * Px);
+      const int k = r >> npsh, p = r & (np - 1);
+      float2 xa = va[u], xb = vb[u];
+      if (k > Px / 2) { xa.y = -xa.y; xb.y = -xb.y; }
+      fbuf[fidx(cc * np + p, k, pitch)] = make_float2(xa.x - xb.y, xa.y + xb.x);
+    }
   }
   __syncthreads();
   block_fft<true>(fbuf, d.plan_x, nc * np, tw);
+  const float rtn = 1.0f / (float)(g.ty * nx), rnx = 1.0f / (float)nx;   // exact quotients (e < 2^22)
   for (int e = threadIdx.x; e < nc * g.ty * nx; e += blockDim.x) {
-    const int cc = e / (g.ty * nx), r = e - cc * (g.ty * nx);
-    const int row = r / nx, x = r - row * nx;
+    const int cc = (int)(((float)e + 0.5f) * rtn), r = e - cc * (g.ty * nx);
+    const int row = (int)(((float)r + 0.5f) * rnx), x = r - row * nx;
     float2 v = fbuf[fidx(cc * np + (row >> 1), x, pitch)];
     bd[((c0 + cc) * g.ty + row) * nx + x] = (row & 1) ? v.y : v.x;
   }

@@ -47,20 +47,53 @@ __device__ __forceinline__ void passA_components(int c0, int nc, float2* fbuf, c
   const int pitch = fft_pitch(Px);
   const int np = g.ty >> 1;
   const long long n = g.n;
-  for (int e = threadIdx.x; e < nc * np * Px; e += blockDim.x) {
-    const int t = e / Px, x = e - t * Px;
-    const int cc = t / np, p = t - cc * np, c = c0 + cc;
-    float v2[2] = {0.0f, 0.0f};
-    if (x < nx) {
+  // Groups of FU elements per thread: all loads and sums of a group first,
+  // then its stores, so that the loads of the group are in flight together
+  // (stores to the stage state would otherwise order every load after the
+  // previous element's stores).  Same arithmetic per element.
+  constexpr int FU = 4;
+  const int total = nc * np * Px;
+  // e / Px by the FP32 quotient of e + 1/2: it is at least 1/(2 Px) from an
+  // integer and its rounding error (e / Px) 2^-23 is smaller for e < 2^22,
+  // so it truncates exactly; np = ty / 2 is a power of two
+  const float rPx = 1.0f / (float)Px;
+  const int npsh = __ffs(np) - 1;
+  for (int e0 = threadIdx.x; e0 < total; e0 += FU * blockDim.x) {
+    float mv[FU][2][NSUB];
+    long long cl[FU][2];
+    int cidx[FU];
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int t = (int)(((float)e + 0.5f) * rPx), x = e - t * Px;
+      const int cc = t >> npsh, p = t & (np - 1), c = c0 + cc;
+      cidx[u] = c;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int row = 2 * p + h, y = y0 + row;
-        if (y >= ny) continue;
-        const long long cell = x + (long long)nx * (y + (long long)ny * z);
+        const int y = y0 + 2 * p + h;
+        const bool ok = e < total && x < nx && y < ny;
+        cl[u][h] = ok ? x + (long long)nx * (y + (long long)ny * z) : -1;
+#pragma unroll
+        for (int s = 0; s < NSUB; ++s) mv[u][h][s] = ok ? stage_value<ASSEMBLE>(a, n, s, c, cl[u][h]) : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= total) continue;
+      const int t = (int)(((float)e + 0.5f) * rPx), x = e - t * Px;
+      const int p = t & (np - 1);
+      const int c = cidx[u];
+      float v2[2] = {0.0f, 0.0f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long cell = cl[u][h];
+        if (cell < 0) continue;
+        const int row = 2 * p + h;
         const int reg = co.uniform ? 0 : co.regions[cell];
 #pragma unroll
         for (int s = 0; s < NSUB; ++s) {
-          float m = stage_value<ASSEMBLE>(a, n, s, c, cell);
+          float m = mv[u][h][s];
           if (ASSEMBLE) {
             if (a.normalize) m *= inv[(s * g.ty + row) * nx + x];
             a.stage[(long long)(3 * s + c) * n + cell] = m;
@@ -68,14 +101,17 @@ __device__ __forceinline__ void passA_components(int c0, int nc, float2* fbuf, c
           v2[h] = fmaf(co.reg[s * MMP_MAX_REGIONS + reg].ms, m, v2[h]);
         }
       }
+      fbuf[fidx(t, x, pitch)] = make_float2(v2[0], v2[1]);
     }
-    fbuf[fidx(t, x, pitch)] = make_float2(v2[0], v2[1]);
   }
   __syncthreads();
   block_fft<false>(fbuf, d.plan_x, nc * np, tw);
-  for (int e = threadIdx.x; e < nc * g.kxn * g.ty; e += blockDim.x) {
-    const int cc = e / (g.kxn * g.ty), r = e - cc * (g.kxn * g.ty);
-    const int k = r / g.ty, row = r - k * g.ty, y = y0 + row;
+  const int kt = g.kxn * g.ty;
+  const float rkt = 1.0f / (float)kt;           // exact quotient as above (e < 2^22)
+  const int tysh = __ffs(g.ty) - 1;
+  for (int e = threadIdx.x; e < nc * kt; e += blockDim.x) {
+    const int cc = (int)(((float)e + 0.5f) * rkt), r = e - cc * kt;
+    const int k = r >> tysh, row = r & (g.ty - 1), y = y0 + row;
     if (y >= ny) continue;
     const int t = cc * np + (row >> 1);
     float2 Z = fbuf[fidx(t, k, pitch)];
