@@ -107,7 +107,17 @@ enum mmp_term {
     MMP_T_ELASTIC = 128  /* elastodynamics rho u'' = f_tot (Eq. elasticity) */
 };
 
-enum mmp_method { MMP_DP45 = 0 };
+/* Embedded Runge-Kutta solvers of the paper's table (Methods): convergence
+ * order / error-estimate order.  The higher-order solution is propagated;
+ * every step ends with an evaluation at the renormalised solution, which is
+ * the next step's first stage (free for the FSAL methods DP45 and BS23). */
+enum mmp_method {
+    MMP_DP45 = 0,      /* Dormand-Prince 5 / 4, 6 evaluations per step */
+    MMP_HEUN = 1,      /* Heun 2 / Euler 1, 2 evaluations per step */
+    MMP_BS23 = 2,      /* Bogacki-Shampine 3 / 2, 3 evaluations per step */
+    MMP_CASHKARP = 3,  /* Cash-Karp 5 / 4, 6 evaluations per step */
+    MMP_RKF45 = 4      /* Fehlberg 5 / 4, 6 evaluations per step */
+};
 
 typedef void* (*mmp_alloc_fn)(size_t bytes, void* user);
 typedef void (*mmp_free_fn)(void* ptr, void* user);
@@ -149,9 +159,11 @@ int mmp_get_m(mmp_ctx* ctx, int sub, float* m);
 int mmp_set_elastic(mmp_ctx* ctx, const float* u, const float* v);
 int mmp_get_elastic(mmp_ctx* ctx, float* u, float* v);
 
-/* Solver.  method = MMP_DP45.  adaptive = 0: fixed step dt.  adaptive = 1:
- * dt is the initial step, tol the absolute max-norm tolerance on the error
- * estimate dt*max|sum_i (b_i - b*_i) k_i| of m, dt in [dt_min, dt_max]. */
+/* Solver.  method: an mmp_method.  adaptive = 0: fixed step dt.  adaptive =
+ * 1: dt is the initial step, tol the absolute max-norm tolerance on the
+ * error estimate dt*max|sum_i (b_i - b*_i) k_i| of m, dt in [dt_min,
+ * dt_max], step factor 0.9 (tol/err)^(1/(q+1)) in [0.2, 5] with q the
+ * method's error-estimate order. */
 int mmp_set_solver(mmp_ctx* ctx, int method, int adaptive, double dt, double tol,
                    double dt_min, double dt_max);
 

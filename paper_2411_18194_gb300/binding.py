@@ -23,6 +23,7 @@ STATUS = {0: "MMP_OK", -1: "MMP_E_INVAL", -2: "MMP_E_OOM", -3: "MMP_E_CUDA", -4:
           -5: "MMP_E_TIMEOUT", -6: "MMP_E_STATE"}
 
 GOALS = {"steps": 0, "run": 1, "relax": 2}
+METHODS = {"DP45": 0, "HEUN": 1, "BS23": 2, "CASHKARP": 3, "RKF45": 4}
 TUNE_BATCH, TUNE_FORCE = 1, 2
 
 
@@ -253,8 +254,8 @@ class Magnet:
         return u, v
 
     # -------------------------------------------------------------- solver --
-    def set_solver(self, adaptive=False, dt=1e-13, tol=1e-5, dt_min=1e-18, dt_max=1e-11):
-        _check(library().mmp_set_solver(self._ctx, 0, int(bool(adaptive)), dt, tol, dt_min, dt_max))
+    def set_solver(self, adaptive=False, dt=1e-13, tol=1e-5, dt_min=1e-18, dt_max=1e-11, method="DP45"):
+        _check(library().mmp_set_solver(self._ctx, METHODS[method], int(bool(adaptive)), dt, tol, dt_min, dt_max))
 
     def eval_field(self, sub=0, B=None, tau=None):
         _check(library().mmp_eval_field(self._ctx, sub, _ptr(B), _ptr(tau)))

@@ -6,7 +6,7 @@
 namespace mmp {
 
 template <bool ASSEMBLE>
-__global__ void __launch_bounds__(kBatchThreads) k_batch_passA(const BatchInst* __restrict__ insts,
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_passA(const BatchInst* __restrict__ insts,
                                                                const BatchItem* __restrict__ items, int stage) {
   extern __shared__ __align__(16) unsigned char sraw[];
   __shared__ BatchInst si;

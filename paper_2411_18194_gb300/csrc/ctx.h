@@ -53,6 +53,7 @@ struct mmp_ctx {
   int ks = 1;                  // pass B stages the kernel slice in shared memory
   int radix_x = 0, radix_y = 0;   // FFT plan variants (make_plan)
   // solver
+  int method = 0;              // MMP_DP45, ... (dp45.h tableau)
   int adaptive = 0;
   double dt = 1e-13, tol = 1e-5, dt_min = 1e-18, dt_max = 1e-11;
   double t = 0.0;

@@ -352,6 +352,10 @@ bool shape_ok(const mmp_ctx* ctx, const mmp_shape& s, const char** why) {
     *why = "unsupported FFT plan";
     return false;
   }
+  if ((long long)(s.ty / 2) * g.Px > (long long)fft_cap_a(px) * 512) {
+    *why = "pass A row pairs above the FFT capacity of a 512-thread block";
+    return false;
+  }
   if (passb_smem(g.ny, g.nz, g.Py, g.kzn, s.R, s.stage_kernel != 0).total > 227 * 1024) {
     *why = "pass B shared memory above 227 KB";
     return false;
@@ -378,7 +382,7 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
   // all three components in one x-FFT call when a 512-thread block holds
   // them and the shared memory of passes A and C fits
   g.xb = 3;
-  if ((long long)3 * (g.ty / 2) * g.Px > (long long)fft_cap(ctx->plan_x) * 512 ||
+  if ((long long)3 * (g.ty / 2) * g.Px > (long long)fft_cap_a(ctx->plan_x) * 512 ||
       smem_passA(g) + (size_t)ctx->nsub * g.ty * g.nx * sizeof(float) > 227 * 1024 ||
       smem_field(g, true) > 227 * 1024)
     g.xb = 1;
@@ -514,24 +518,27 @@ int ensure_k1(mmp_ctx* ctx, int relax) {
   return MMP_OK;
 }
 
-// One DP45 attempt of size h.  With want_err the error estimate (and the
-// torque maximum at the new state) are read back (one synchronisation).
+// One attempt of size h of the context's method: stages 1..S, the last at
+// the renormalised solution (whose k is the next step's k1).  With want_err
+// the error estimate (and the torque maximum at the new state) are read
+// back (one synchronisation).
 int attempt(mmp_ctx* ctx, double h, bool want_err, int relax, double* err_out, double* tmax_out) {
   TRY(ensure_k1(ctx, relax));
   if (want_err) CK(cudaMemsetAsync(ctx->d_red, 0, 2 * sizeof(unsigned), ctx->stream), "reset error");
+  const Tableau& T = tableau(ctx->method);
   float ecoef[7];
-  error_coefs(h, ecoef);
+  error_coefs(T, h, ecoef);
   const float* ek[6];
-  for (int j = 0; j < 6; ++j) ek[j] = ctx->d_k[j];
-  for (int i = 1; i <= 6; ++i) {
+  for (int j = 0; j < 6; ++j) ek[j] = j < T.S ? ctx->d_k[j] : nullptr;
+  for (int i = 1; i <= T.S; ++i) {
     StageArgs sa;
     memset(&sa, 0, sizeof sa);
     sa.y = ctx->d_y;
     sa.nk = i;
     for (int j = 0; j < i; ++j) sa.k[j] = ctx->d_k[j];
-    stage_coefs(h, i, sa.coef);
-    sa.normalize = (i == 6);
-    bool last = (i == 6);
+    stage_coefs(T, h, i, sa.coef);
+    sa.normalize = (i == T.S);
+    bool last = (i == T.S);
     TRY(evaluate(ctx, sa, nullptr, ctx->d_k[i], nullptr, last && want_err ? ctx->d_red : nullptr, ecoef, ek,
                  relax, last && want_err ? ctx->d_red + 1 : nullptr));
   }
@@ -550,7 +557,7 @@ int attempt(mmp_ctx* ctx, double h, bool want_err, int relax, double* err_out, d
 
 void accept(mmp_ctx* ctx, double h) {
   std::swap(ctx->d_y, ctx->d_stage);
-  std::swap(ctx->d_k[0], ctx->d_k[6]);
+  std::swap(ctx->d_k[0], ctx->d_k[tableau(ctx->method).S]);
   ctx->k1_valid = true;
   ctx->t += h;
   ctx->steps++;
@@ -585,7 +592,7 @@ int advance(mmp_ctx* ctx, long long nsteps, double until, int relax, double torq
       return fail(MMP_E_NONFINITE, "non-finite error estimate at t = %g s (dt = %g s)", ctx->t, h);
     }
     bool ok = err <= ctx->tol || h <= ctx->dt_min;
-    double fac = grow(err, ctx->tol);
+    double fac = grow(err, ctx->tol, tableau(ctx->method).exponent);
     if (ok) {
       accept(ctx, h);
       ++done;
@@ -694,7 +701,7 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
   g.Px = nice_length(nx); g.Py = nice_length(ny); g.Pz = nice_length(nz);
   g.kxn = g.Px / 2 + 1; g.kyn = g.Py / 2 + 1; g.kzn = g.Pz / 2 + 1;
   g.krow = (6 * g.kzn + 3) & ~3;
-  g.ty = pick_tile_rows(g.ny, g.nz);
+  g.ty = pick_tile_rows(g.ny, g.nz, g.Px);
   g.xb = 1;
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (float)ctx->cell[a];
@@ -712,7 +719,7 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
   CR(upload_table(ctx, ctx->d_tw_z, roots(g.Pz)));
   if (rc == MMP_OK) {
     mmp_shape sh;
-    sh.ty = pick_tile_rows(g.ny, g.nz);
+    sh.ty = pick_tile_rows(g.ny, g.nz, g.Px);
     sh.radix_x = 0;
     sh.radix_y = 0;
     sh.R = pick_residues(g);
@@ -874,9 +881,11 @@ int mmp_get_elastic(mmp_ctx* ctx, float* u, float* v) {
 
 int mmp_set_solver(mmp_ctx* ctx, int method, int adaptive, double dt, double tol, double dt_min, double dt_max) {
   TRY(check_ctx(ctx));
-  if (method != MMP_DP45) return fail(MMP_E_INVAL, "unknown method %d", method);
+  if (method < MMP_DP45 || method > MMP_RKF45) return fail(MMP_E_INVAL, "unknown method %d", method);
   if (!(dt > 0) || !(dt_min > 0) || !(dt_max >= dt_min) || (adaptive && !(tol > 0)))
     return fail(MMP_E_INVAL, "bad solver settings");
+  if (method != ctx->method) ctx->k1_valid = false;
+  ctx->method = method;
   ctx->adaptive = adaptive ? 1 : 0;
   ctx->dt = dt;
   ctx->tol = tol;
@@ -1060,7 +1069,8 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
   if (batch) {
     start.R = 1;
     start.stage_kernel = 0;
-    start.ty = 8;
+    start.ty = 8;   // the largest tiles that fit
+    while (start.ty > 2 && !shape_ok(ctx, start, &why)) start.ty >>= 1;
     if (!shape_ok(ctx, start, &why)) return fail(MMP_E_INVAL, "no batch shape fits this grid: %s", why);
   }
   TRY(apply_shape(ctx, start));
@@ -1075,7 +1085,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
   std::vector<mmp_shape> cand_ac, cand_b;
   for (int ty : {2, 4, 8})
     for (int rx = 0; rx < 2; ++rx) {
-      if (batch && ty != 8) continue;   // a batch gets its parallelism from its members
+      if (batch && ty != start.ty) continue;   // a batch gets its parallelism from its members
       mmp_shape s = start;
       s.ty = ty;
       s.radix_x = rx;

@@ -99,7 +99,7 @@ int set_up(Setup& S, int nx, int ny, int nz, const double* cell, cudaStream_t s)
   g.Px = nice_length(nx); g.Py = nice_length(ny); g.Pz = nice_length(nz);
   g.kxn = g.Px / 2 + 1; g.kyn = g.Py / 2 + 1; g.kzn = g.Pz / 2 + 1;
   g.krow = (6 * g.kzn + 3) & ~3;
-  g.ty = pick_tile_rows(g.ny, g.nz);
+  g.ty = pick_tile_rows(g.ny, g.nz, g.Px);
   g.xb = 1;
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (float)cell[a];

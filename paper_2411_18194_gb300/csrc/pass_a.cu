@@ -29,7 +29,7 @@ __global__ void k_normalize(float* m, long long n) {
 }
 
 template <int NSUB, bool ASSEMBLE>
-__global__ void __launch_bounds__(512) k_passA(Grid g, StageArgs a, DemagArgs d, Coefs co) {
+__global__ void __launch_bounds__(512, 2) k_passA(Grid g, StageArgs a, DemagArgs d, Coefs co) {
   extern __shared__ __align__(16) unsigned char sraw[];
   passA_tile<NSUB, ASSEMBLE>(sraw, g, a, d, co, blockIdx.y, blockIdx.x * g.ty);
 }

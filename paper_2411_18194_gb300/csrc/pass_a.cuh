@@ -9,6 +9,11 @@
 namespace mmp {
 
 // ------------------------------------------------------------- pass A ----
+// Pass A runs two 512-thread blocks per SM (64 registers a thread): its time
+// goes to waiting on the stage loads, so twice the warps hide more of it.
+// Its FFT therefore holds 16 values per thread (15 with a radix-3 pass),
+// half of the other passes' (fft_cap_a on the host).
+constexpr int kCapA = 16;
 // Shared memory: the row-pair FFT buffer (padded layout) of xb components,
 // the length-Px twiddles, and for the renormalised stage 1/|m_i| of every
 // tile cell and sublattice.
@@ -51,7 +56,7 @@ __device__ __forceinline__ void passA_components(int c0, int nc, float2* fbuf, c
   // then its stores, so that the loads of the group are in flight together
   // (stores to the stage state would otherwise order every load after the
   // previous element's stores).  Same arithmetic per element.
-  constexpr int FU = 4;
+  constexpr int FU = 2;
   const int total = nc * np * Px;
   // e / Px by the FP32 quotient of e + 1/2: it is at least 1/(2 Px) from an
   // integer and its rounding error (e / Px) 2^-23 is smaller for e < 2^22,
@@ -105,7 +110,7 @@ __device__ __forceinline__ void passA_components(int c0, int nc, float2* fbuf, c
     }
   }
   __syncthreads();
-  block_fft<false>(fbuf, d.plan_x, nc * np, tw);
+  block_fft<false, kCapA>(fbuf, d.plan_x, nc * np, tw);
   const int kt = g.kxn * g.ty;
   const float rkt = 1.0f / (float)kt;           // exact quotient as above (e < 2^22)
   const int tysh = __ffs(g.ty) - 1;

@@ -94,6 +94,9 @@ inline int fft_cap(int L) {
   FftPlan p;
   return make_plan(L, p) ? fft_cap(p) : 32;
 }
+// Pass A holds half of that (kCapA = 16 values a thread, two blocks per SM).
+inline int fft_cap_a(const FftPlan& p) { return fft_cap(p) / 2; }
+inline int fft_cap_a(int L) { return fft_cap(L) / 2; }
 
 inline std::vector<float2> roots(int P) {
   std::vector<float2> w(P);
@@ -119,10 +122,12 @@ inline int pick_residues(const Grid& g) {
 }
 
 // Rows per tile of passes A and C: 8, or fewer (down to one row pair) while
-// the grid would give fewer than two tiles per SM of the 152.
-inline int pick_tile_rows(int ny, int nz) {
+// the grid would give fewer than two tiles per SM of the 152, or while pass
+// A's row pairs exceed what a 512-thread block of it holds.
+inline int pick_tile_rows(int ny, int nz, int Px) {
   int ty = 8;
   while (ty > 2 && (long long)((ny + ty - 1) / ty) * nz < 2 * 152) ty >>= 1;
+  while (ty > 2 && (long long)(ty / 2) * Px > (long long)fft_cap_a(Px) * 512) ty >>= 1;
   return ty;
 }
 
@@ -133,7 +138,8 @@ inline void launch_threads(const Grid& g, int R, int* thrA, int* thrB, int* thrC
   auto need = [](long long el, int cap) { return (el + cap - 1) / cap; };
   const int np = g.ty >> 1;
   const long long fx = need((long long)g.xb * np * g.Px, fft_cap(g.Px));
-  *thrA = std::min(512, std::max(128, r32(fx)));
+  const long long fa = need((long long)g.xb * np * g.Px, fft_cap_a(g.Px));
+  *thrA = std::min(512, std::max(128, r32(fa)));
   const int Ly = g.Py / R;
   const long long elB = (long long)3 * g.nz * Ly;
   *thrB = std::min(512, std::max(64, r32(std::max(need(elB, fft_cap(Ly)), (long long)Ly))));

@@ -63,6 +63,10 @@ def test_binding_ids_match_header_enums():
         assert enums["MMP_" + name] == v
     for name, v in binding.TERM_BITS.items():
         assert enums["MMP_T_" + name] == v
+    for name, v in binding.METHODS.items():
+        assert enums["MMP_" + name] == v
+    for name, v in binding.GOALS.items():
+        assert enums["MMP_GOAL_" + name.upper()] == v
 
 
 def test_create_rejects_bad_arguments_before_touching_the_device():
@@ -75,3 +79,56 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     rc = lib.mmp_create(ctypes.byref(ctx), 4, 4, 4, 1e-9, 1e-9, 1e-9, 3, None, binding.ALLOC_FN(),
                         binding.FREE_FN(), None)
     assert rc == -1 and b"sublattices" in lib.mmp_last_error()
+
+
+def test_host_tableaux_equal_the_oracle_fractions():
+    """The library's FP64 tableaux (csrc/dp45.h, compiled here with g++) equal
+    the oracle's exact fractions to double rounding, for every method."""
+    import shutil
+    import subprocess
+    import tempfile
+    from oracle.dp45 import METHODS
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    src = r'''
+#include <cstdio>
+#include "dp45.h"
+int main() {
+  for (int m = 0; m < 5; ++m) {
+    const mmp::Tableau& T = mmp::tableau(m);
+    std::printf("%d %d %.17g\n", m, T.S, T.exponent);
+    for (int i = 1; i <= T.S; ++i)
+      for (int j = 0; j < i; ++j) std::printf("a %d %d %d %.17g\n", m, i, j, T.a[i][j]);
+    for (int j = 0; j <= T.S; ++j) std::printf("e %d %d %.17g\n", m, j, T.e[j]);
+  }
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.cpp")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call([gxx, "-std=c++17", "-I", os.path.join(ROOT, "paper_2411_18194_gb300", "csrc"),
+                               c, "-o", exe])
+        out = subprocess.check_output([exe], text=True).split("\n")
+    ids = {0: "DP45", 1: "HEUN", 2: "BS23", 3: "CASHKARP", 4: "RKF45"}
+    seen = 0
+    for line in out:
+        f = line.split()
+        if not f:
+            continue
+        if f[0] == "a":
+            m, i, j, v = ids[int(f[1])], int(f[2]), int(f[3]), float(f[4])
+            row = METHODS[m]["A"][i]
+            ref = float(row[j]) if j < len(row) else 0.0
+            assert abs(v - ref) <= 4e-16 * max(1.0, abs(ref)), (m, i, j, v, ref)
+            seen += 1
+        elif f[0] == "e":
+            m, j, v = ids[int(f[1])], int(f[2]), float(f[3])
+            ref = float(METHODS[m]["E"][j])
+            assert abs(v - ref) <= 4e-16 * max(1.0, abs(ref)) + 1e-17, (m, j, v, ref)
+            seen += 1
+        else:
+            m = ids[int(f[0])]
+            assert int(f[1]) == METHODS[m]["S"] and float(f[2]) == METHODS[m]["exponent"]
+    assert seen > 50

@@ -200,3 +200,30 @@ def test_c2_full_size_sampled_parity():
         ref = bd + local[:, z, y, x]
         got = Bg[0][:, z, y, x]
         assert np.abs(got - ref).max() <= bar, ((x, y, z), got, ref)
+
+
+@pytest.mark.parametrize("method", ["HEUN", "BS23", "CASHKARP", "RKF45"])
+def test_other_embedded_solvers_match_oracle(method):
+    """The other solvers of the paper's table: a fixed-step trajectory and an
+    adaptive run against the oracle with the same method."""
+    from oracle.dp45 import Oracle, State
+    w = config_small((20, 16, 2), (2e-9, 2e-9, 1e-9), 91)
+    p = w.problem
+    dt = 2e-15 if method == "HEUN" else 1e-14
+    mag = make_magnet(p, w.m0)
+    mag.set_solver(adaptive=False, dt=dt, method=method)
+    mag.step(15)
+    st = Oracle(p, method=method).run_fixed(State(w.m0), dt, 15)
+    assert np.abs(_get_m(mag, p) - st.ms[0]).max() <= 1e-4
+    S = {"HEUN": 2, "BS23": 3, "CASHKARP": 6, "RKF45": 6}[method]
+    assert mag.time()["evals"] == 1 + S * 15
+    mag.close()
+    mag = make_magnet(p, w.m0)
+    mag.set_solver(adaptive=True, dt=1e-15, tol=1e-5, method=method)
+    mag.run(5e-12)
+    st, stats = Oracle(p, method=method).run_adaptive(State(w.m0), 1e-15, 1e-5, 5e-12)
+    info = mag.time()
+    assert info["t"] == pytest.approx(5e-12, rel=1e-12)
+    assert abs(info["steps"] - stats["accepted"]) <= max(2, 0.05 * stats["accepted"])
+    assert np.abs(_get_m(mag, p) - st.ms[0]).max() <= 1e-4
+    mag.close()
