@@ -71,7 +71,8 @@ enum mmp_param {
     MMP_DIND = 6,   /* interfacial DMI strength D (J/m^2) */
     MMP_B1 = 7,     /* first magnetoelastic coupling constant (J/m^3) */
     MMP_B2 = 8,     /* second magnetoelastic coupling constant (J/m^3) */
-    MMP_NPARAM = 9
+    MMP_KC1 = 9,    /* cubic anisotropy constant (J/m^3) along the axes ANIS_C1, ANIS_C2 */
+    MMP_NPARAM = 10
 };
 
 /* Per-sublattice, per-region vector parameters (mmp_set_param3). */
@@ -79,7 +80,10 @@ enum mmp_param3 {
     MMP_ANIS_U = 0,   /* uniaxial axis of KU1/KU2 (normalised by the library) */
     MMP_ANIS_UB = 1,  /* uniaxial axis of KB1 (normalised by the library) */
     MMP_B_EXT = 2,    /* external field (T) */
-    MMP_NPARAM3 = 3
+    MMP_ANIS_C1 = 3,  /* first cubic axis (normalised; default x) */
+    MMP_ANIS_C2 = 4,  /* second cubic axis (made orthogonal to C1 and normalised; default y);
+                         the third is C1 x C2 */
+    MMP_NPARAM3 = 5
 };
 
 /* Global constants (mmp_set_global). */
@@ -104,7 +108,10 @@ enum mmp_term {
     MMP_T_ZEEMAN = 16,   /* external field B_EXT */
     MMP_T_AFM = 32,      /* A12 and A0 terms of Eq. AFM_exchange_field (2 sublattices) */
     MMP_T_MEL = 64,      /* magnetoelastic field/force (Eqs. magnetoelastic-field/-force) */
-    MMP_T_ELASTIC = 128  /* elastodynamics rho u'' = f_tot (Eq. elasticity) */
+    MMP_T_ELASTIC = 128, /* elastodynamics rho u'' = f_tot (Eq. elasticity) */
+    MMP_T_CUBIC = 256    /* cubic anisotropy: energy Kc1 (a^2 b^2 + a^2 c^2 + b^2 c^2), a, b, c the
+                            components of m on the cubic axes (the paper's "uniaxial or cubic"
+                            anisotropy, as in mumax3) */
 };
 
 /* Embedded Runge-Kutta solvers of the paper's table (Methods): convergence

@@ -19,10 +19,10 @@ MU0 = 4e-7 * np.pi         # vacuum permeability, T m / A
 N_REGIONS = 256
 
 # Per-sublattice, per-region scalar and vector parameters.
-PARAM_SCALARS = ("MS", "AEX", "ALPHA", "KU1", "KU2", "KB1", "DIND", "B1", "B2")
-PARAM_VECTORS = ("ANIS_U", "ANIS_UB", "B_EXT")
+PARAM_SCALARS = ("MS", "AEX", "ALPHA", "KU1", "KU2", "KB1", "DIND", "B1", "B2", "KC1")
+PARAM_VECTORS = ("ANIS_U", "ANIS_UB", "B_EXT", "ANIS_C1", "ANIS_C2")
 GLOBALS = ("A0", "A12", "LATTICE_A", "C11", "C12", "C44", "RHO", "ETA")
-TERMS = ("DEMAG", "EXCH", "ANIS", "DMI", "ZEEMAN", "AFM", "MEL", "ELASTIC")
+TERMS = ("DEMAG", "EXCH", "ANIS", "DMI", "ZEEMAN", "AFM", "MEL", "ELASTIC", "CUBIC")
 
 
 @dataclass
@@ -43,8 +43,10 @@ class Problem:
             v = np.zeros((self.n_sub, N_REGIONS, 3))
             if k == "ANIS_U":
                 v[..., 2] = 1.0
-            if k == "ANIS_UB":
+            if k in ("ANIS_UB", "ANIS_C1"):
                 v[..., 0] = 1.0
+            if k == "ANIS_C2":
+                v[..., 1] = 1.0
             self.vec.setdefault(k, v)
         for k in GLOBALS:
             self.glob.setdefault(k, 0.0)
@@ -179,6 +181,16 @@ def config_small(shape, cell, seed, terms=("DEMAG", "EXCH", "ANIS", "DMI", "ZEEM
             p.set("B_EXT", (0.02 * r[k % 64], -0.01, 0.05), s, reg); k += 1
             p.set("B1", -1e7 * r[k % 64], s, reg); k += 1
             p.set("B2", -5e6 * r[k % 64], s, reg); k += 1
+    # cubic anisotropy parameters from their own stream (the draws above keep
+    # their values); the axes are not orthogonal on purpose
+    r2 = _rand_params(seed + 101, 8 * n_regions * n_sub + 8)
+    k2 = 0
+    for reg in range(n_regions):
+        for s in range(n_sub):
+            p.set("KC1", 5e4 * (r2[k2] - 0.3), s, reg)
+            p.set("ANIS_C1", (1.0, r2[k2 + 1] - 0.5, r2[k2 + 2] - 0.5), s, reg)
+            p.set("ANIS_C2", (r2[k2 + 3] - 0.5, 1.0, r2[k2 + 4] - 0.5), s, reg)
+            k2 += 5
     if n_regions > 1 or empty_fraction > 0:
         p.set("MS", 0.0, None, 255)
     p.glob.update(A0=-4e-11, A12=-1e-12, LATTICE_A=0.42e-9, C11=2.5e11,

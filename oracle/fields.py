@@ -48,11 +48,19 @@ def cell_params(p):
     P = {k: p.scal[k][:, reg] for k in PARAM_SCALARS}
     for k in PARAM_VECTORS:
         v = np.moveaxis(p.vec[k][:, reg], -1, 1)
-        if k in ("ANIS_U", "ANIS_UB"):
-            nrm = np.sqrt((v * v).sum(axis=1, keepdims=True))
-            v = np.where(nrm > 0, v / np.where(nrm > 0, nrm, 1.0), 0.0)
+        if k in ("ANIS_U", "ANIS_UB", "ANIS_C1"):
+            v = _unit(v)
         P[k] = v
+    # cubic axes: c2 made orthogonal to c1 (Gram-Schmidt), c3 = c1 x c2
+    c1 = P["ANIS_C1"]
+    P["ANIS_C2"] = _unit(P["ANIS_C2"] - (P["ANIS_C2"] * c1).sum(axis=1, keepdims=True) * c1)
+    P["ANIS_C3"] = np.cross(c1, P["ANIS_C2"], axis=1)
     return P
+
+
+def _unit(v):
+    nrm = np.sqrt((v * v).sum(axis=1, keepdims=True))
+    return np.where(nrm > 0, v / np.where(nrm > 0, nrm, 1.0), 0.0)
 
 
 def shift(a, axis, d):
@@ -160,6 +168,18 @@ def anisotropy_field(p, P, s, m):
                   + 2.0 * P["KB1"][s] * mub * ub)
 
 
+def cubic_anisotropy_field(p, P, s, m):
+    """Cubic anisotropy (the paper's field terms: uniaxial or cubic, done as in
+    mumax3): energy density Kc1 (a^2 b^2 + a^2 c^2 + b^2 c^2) with a, b, c the
+    components of m along the cubic axes c1, c2, c3; field -(1/Ms) dE/dm."""
+    Ms = P["MS"][s]
+    inv = np.where(Ms > 0, 1.0 / np.where(Ms > 0, Ms, 1.0), 0.0)
+    c1, c2, c3 = P["ANIS_C1"][s], P["ANIS_C2"][s], P["ANIS_C3"][s]
+    a, b, c = _dot(m, c1), _dot(m, c2), _dot(m, c3)
+    K = P["KC1"][s]
+    return -2.0 * K * inv * (a * (b * b + c * c) * c1 + b * (a * a + c * c) * c2 + c * (a * a + b * b) * c3)
+
+
 def afm_field(p, P, s, ms):
     """Intersublattice exchange for sublattice s: (A12/Ms) lap(m') with
     zero-Neumann ghosts + (4 A0 / (Ms a^2)) m'."""
@@ -224,6 +244,8 @@ def effective_fields(p, ms, u=None, noct=None, demag="fft", P=None, parts=False)
             d["dmi"] = dmi_field(p, P, s, m)
         if "ANIS" in terms:
             d["anis"] = anisotropy_field(p, P, s, m)
+        if "CUBIC" in terms:
+            d["cubic"] = cubic_anisotropy_field(p, P, s, m)
         if "ZEEMAN" in terms:
             d["zeeman"] = P["B_EXT"][s] * np.ones_like(m)
         if "AFM" in terms and p.n_sub == 2:
@@ -279,6 +301,10 @@ def energies(p, ms, u=None, noct=None, P=None):
             mu, mub = _dot(m, P["ANIS_U"][s]), _dot(m, P["ANIS_UB"][s])
             e = -P["KU1"][s] * mu ** 2 - P["KU2"][s] * mu ** 4 - P["KB1"][s] * mub ** 2
             E["anis"] = E.get("anis", 0.0) + dV * np.where(Ms > 0, e, 0.0).sum()
+        if "CUBIC" in terms:
+            a, b, c = (_dot(m, P[k][s]) for k in ("ANIS_C1", "ANIS_C2", "ANIS_C3"))
+            e = P["KC1"][s] * (a * a * b * b + a * a * c * c + b * b * c * c)
+            E["cubic"] = E.get("cubic", 0.0) + dV * np.where(Ms > 0, e, 0.0).sum()
         if "ZEEMAN" in terms:
             E["zeeman"] = E.get("zeeman", 0.0) - dV * (Ms * _dot(m, P["B_EXT"][s])).sum()
         if "MEL" in terms:

@@ -15,9 +15,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_lib", "libmmp.so")
 
 TERM_BITS = {"DEMAG": 1, "EXCH": 2, "ANIS": 4, "DMI": 8, "ZEEMAN": 16, "AFM": 32, "MEL": 64,
-             "ELASTIC": 128}
-PARAM_IDS = {"MS": 0, "AEX": 1, "ALPHA": 2, "KU1": 3, "KU2": 4, "KB1": 5, "DIND": 6, "B1": 7, "B2": 8}
-PARAM3_IDS = {"ANIS_U": 0, "ANIS_UB": 1, "B_EXT": 2}
+             "ELASTIC": 128, "CUBIC": 256}
+PARAM_IDS = {"MS": 0, "AEX": 1, "ALPHA": 2, "KU1": 3, "KU2": 4, "KB1": 5, "DIND": 6, "B1": 7, "B2": 8,
+             "KC1": 9}
+PARAM3_IDS = {"ANIS_U": 0, "ANIS_UB": 1, "B_EXT": 2, "ANIS_C1": 3, "ANIS_C2": 4}
 GLOBAL_IDS = {"A0": 0, "A12": 1, "LATTICE_A": 2, "C11": 3, "C12": 4, "C44": 5, "RHO": 6, "ETA": 7}
 STATUS = {0: "MMP_OK", -1: "MMP_E_INVAL", -2: "MMP_E_OOM", -3: "MMP_E_CUDA", -4: "MMP_E_NONFINITE",
           -5: "MMP_E_TIMEOUT", -6: "MMP_E_STATE"}

@@ -77,6 +77,8 @@ struct RegionCoef {
   float bext[3];       // external field (T)
   float afm12[3];      // A12 / (Ms h_a^2)
   float2 afm0;         // 4 A0 / (Ms a^2) (hi, lo)
+  float kc1;           // 2 Kc1 / Ms (cubic anisotropy)
+  float c1[3], c2[3], c3[3];   // cubic axes (orthonormal)
   float mel1, mel2;    // -2 B1 / Ms, -2 B2 / Ms
   float b1, b2;        // B1, B2 (J/m^3) for the magnetoelastic force
 };

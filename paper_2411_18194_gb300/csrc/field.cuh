@@ -125,6 +125,16 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
 #pragma unroll
     for (int i = 0; i < 3; ++i) sm[i] = fmaf(c1, R.u[i], fmaf(c2, R.ub[i], sm[i]));
   }
+  if (terms & 256u) {   // cubic anisotropy: -(2 Kc1/Ms) [a (b^2 + c^2) c1 + b (a^2 + c^2) c2 + c (a^2 + b^2) c3]
+    const float ca = m[0] * R.c1[0] + m[1] * R.c1[1] + m[2] * R.c1[2];
+    const float cb = m[0] * R.c2[0] + m[1] * R.c2[1] + m[2] * R.c2[2];
+    const float cc = m[0] * R.c3[0] + m[1] * R.c3[1] + m[2] * R.c3[2];
+    const float fa = -R.kc1 * ca * fmaf(cb, cb, cc * cc);
+    const float fb = -R.kc1 * cb * fmaf(ca, ca, cc * cc);
+    const float fc = -R.kc1 * cc * fmaf(ca, ca, cb * cb);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sm[i] = fmaf(fa, R.c1[i], fmaf(fb, R.c2[i], fmaf(fc, R.c3[i], sm[i])));
+  }
   if (terms & 16u) {  // Zeeman
 #pragma unroll
     for (int i = 0; i < 3; ++i) sm[i] += R.bext[i];

@@ -159,6 +159,27 @@ int upload_coefs(mmp_ctx* ctx) {
       c.ku1 = (float)(2.0 * ctx->scal[MMP_KU1][s][r] * im);
       c.ku2 = (float)(4.0 * ctx->scal[MMP_KU2][s][r] * im);
       c.kb1 = (float)(2.0 * ctx->scal[MMP_KB1][s][r] * im);
+      // cubic axes: c1 normalised, c2 made orthogonal to it (Gram-Schmidt), c3 = c1 x c2
+      {
+        const double* a1 = ctx->vec[MMP_ANIS_C1][s][r];
+        const double* a2 = ctx->vec[MMP_ANIS_C2][s][r];
+        double n1 = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+        double e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
+        if (n1 > 0)
+          for (int i = 0; i < 3; ++i) e1[i] = a1[i] / n1;
+        double d12 = a2[0] * e1[0] + a2[1] * e1[1] + a2[2] * e1[2];
+        double v2[3] = {a2[0] - d12 * e1[0], a2[1] - d12 * e1[1], a2[2] - d12 * e1[2]};
+        double n2 = sqrt(v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2]);
+        if (n2 > 0)
+          for (int i = 0; i < 3; ++i) e2[i] = v2[i] / n2;
+        double e3[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        for (int i = 0; i < 3; ++i) {
+          c.c1[i] = (float)e1[i];
+          c.c2[i] = (float)e2[i];
+          c.c3[i] = (float)e3[i];
+        }
+        c.kc1 = (float)(2.0 * ctx->scal[MMP_KC1][s][r] * im);
+      }
       const double* u = ctx->vec[MMP_ANIS_U][s][r];
       const double* ub = ctx->vec[MMP_ANIS_UB][s][r];
       double nu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -695,6 +716,8 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
     for (int r = 0; r < MMP_MAX_REGIONS; ++r) {
       ctx->vec[MMP_ANIS_U][s][r][2] = 1.0;
       ctx->vec[MMP_ANIS_UB][s][r][0] = 1.0;
+      ctx->vec[MMP_ANIS_C1][s][r][0] = 1.0;
+      ctx->vec[MMP_ANIS_C2][s][r][1] = 1.0;
     }
   Grid& g = ctx->g;
   g.nx = nx; g.ny = ny; g.nz = nz; g.n = n;
@@ -825,7 +848,7 @@ int mmp_set_global(mmp_ctx* ctx, int param, double value) {
 
 int mmp_enable_terms(mmp_ctx* ctx, unsigned terms) {
   TRY(check_ctx(ctx));
-  if (terms & ~255u) return fail(MMP_E_INVAL, "unknown term bits 0x%x", terms);
+  if (terms & ~511u) return fail(MMP_E_INVAL, "unknown term bits 0x%x", terms);
   ctx->terms = terms;
   ctx->k1_valid = false;
   return ensure_state(ctx);

@@ -102,10 +102,10 @@ def _fd_field(energy_fn, ms, s, cell_idx, Ms, dV, h=1e-5):
     return out
 
 
-@pytest.mark.parametrize("term", ["demag", "exch", "dmi", "anis", "zeeman"])
+@pytest.mark.parametrize("term", ["demag", "exch", "dmi", "anis", "zeeman", "cubic"])
 def test_field_is_energy_gradient_ferromagnet(term):
     name = {"demag": "DEMAG", "exch": "EXCH", "dmi": "DMI", "anis": "ANIS",
-            "zeeman": "ZEEMAN"}[term]
+            "zeeman": "ZEEMAN", "cubic": "CUBIC"}[term]
     terms = (name, "EXCH") if term == "dmi" else (name,)
     w = config_small((7, 6, 3), (2e-9, 2.5e-9, 1e-9), 11, terms=terms, n_regions=2)
     p = w.problem
@@ -264,3 +264,21 @@ def test_energy_decreases_with_damping():
         st, k, _ = o.attempt(st, k, 2e-14)
         E.append(sum(fields.energies(p, st.ms, noct=o.noct).values()))
     assert np.all(np.diff(E) < 0), np.diff(E)
+
+
+def test_cubic_anisotropy_closed_forms():
+    """Cubic anisotropy: no field along a cubic axis, and along the body
+    diagonal (c1 + c2 + c3)/sqrt(3) the field -(4 Kc1 / (3 Ms)) m, for rotated
+    axes."""
+    p = Problem((2, 1, 1), (1e-9,) * 3, 1, frozenset({"CUBIC"}))
+    Ms, K = 8e5, 3e4
+    rot = np.array([[0.36, 0.48, -0.8], [-0.8, 0.6, 0.0], [0.48, 0.64, 0.6]])   # orthogonal
+    c1, c2, c3 = rot
+    p.set("MS", Ms).set("KC1", K).set("ANIS_C1", tuple(c1)).set("ANIS_C2", tuple(c2))
+    P = fields.cell_params(p)
+    assert np.allclose(P["ANIS_C3"][0][:, 0, 0, 0], np.cross(c1, c2))
+    diag = (c1 + c2 + c3) / np.sqrt(3.0)
+    m = np.stack([c2, diag], axis=1).reshape(3, 1, 1, 2)
+    B = fields.cubic_anisotropy_field(p, P, 0, m)
+    assert np.abs(B[:, 0, 0, 0]).max() < 1e-12
+    assert np.allclose(B[:, 0, 0, 1], -(4.0 * K / (3.0 * Ms)) * diag, rtol=1e-12, atol=0)
