@@ -30,10 +30,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // 3x3 symmetric kernel times a complex 3-vector.  K points at the six
 // components (xx, yy, zz, xy, xz, yz) of octant entry (|ky|, |kz|); sy, sz
 // flip the components odd in ky, kz.
+// KG: K is in global memory (read-only: non-coherent loads that need not wait
+// for earlier shared-memory stores); else in shared memory.
+template <bool KG>
 __device__ __forceinline__ void kmul(const float* K, float sy, float sz, float2& a, float2& b, float2& c) {
-  const float2 k01 = reinterpret_cast<const float2*>(K)[0];
-  const float2 k23 = reinterpret_cast<const float2*>(K)[1];
-  const float2 k45 = reinterpret_cast<const float2*>(K)[2];
+  const float2* K2 = reinterpret_cast<const float2*>(K);
+  const float2 k01 = KG ? __ldg(K2) : K2[0];
+  const float2 k23 = KG ? __ldg(K2 + 1) : K2[1];
+  const float2 k45 = KG ? __ldg(K2 + 2) : K2[2];
   float xx = k01.x, yy = k01.y, zz = k23.x, xy = k23.y * sy, xz = k45.x * sz, yz = k45.y * sy * sz;
   float2 ha = make_float2(xx * a.x + xy * b.x + xz * c.x, xx * a.y + xy * b.y + xz * c.y);
   float2 hb = make_float2(xy * a.x + yy * b.x + yz * c.x, xy * a.y + yy * b.y + yz * c.y);
@@ -49,9 +53,10 @@ __device__ __forceinline__ void dft_small(float2 (&f)[N]) {
 }
 
 // nz = 1: the kernel multiply alone, one thread per column.
+template <bool KG>
 __device__ __forceinline__ void zkz_single(float2* W, int pitch, int kp, const float* Kc, float sy) {
   float2 a = W[fidx(0, kp, pitch)], b = W[fidx(1, kp, pitch)], c = W[fidx(2, kp, pitch)];
-  kmul(Kc, sy, 1.0f, a, b, c);
+  kmul<KG>(Kc, sy, 1.0f, a, b, c);
   W[fidx(0, kp, pitch)] = a; W[fidx(1, kp, pitch)] = b; W[fidx(2, kp, pitch)] = c;
 }
 
@@ -60,7 +65,7 @@ __device__ __forceinline__ void zkz_single(float2* W, int pitch, int kp, const f
 // multiply, inverse DFT_NZ, times w^(-par z); the two lanes add their halves
 // through a shuffle and each writes NZ/2 of the z outputs.  Both lanes read
 // the column before the shuffle, so neither writes before the other read.
-template <int NZ>
+template <int NZ, bool KG>
 __device__ __forceinline__ void zkz_pair(float2* W, int pitch, int kp, bool valid, int par, const float* Kc,
                                          float sy, const float2* __restrict__ twz) {
   float2 f[3][NZ];
@@ -78,7 +83,7 @@ __device__ __forceinline__ void zkz_pair(float2* W, int pitch, int kp, bool vali
     int kz = 2 * q + par;
     int ikz = kz <= NZ ? kz : 2 * NZ - kz;
     float sz = kz <= NZ ? 1.0f : -1.0f;
-    kmul(Kc + ikz * 6, sy, sz, f[0][q], f[1][q], f[2][q]);
+    kmul<KG>(Kc + ikz * 6, sy, sz, f[0][q], f[1][q], f[2][q]);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) dft_small<NZ, true>(f[c]);
@@ -103,6 +108,7 @@ __device__ __forceinline__ void zkz_pair(float2* W, int pitch, int kp, bool vali
 }
 
 // Any nz <= 16: direct DFT over the padded length Pz, one thread per column.
+template <bool KG>
 static __device__ void zkz_generic(float2* W, int kp, int pitch, int nz, int Pz, const float* Kc, float sy,
                             const float2* __restrict__ twz) {
   float2 out[3][16];
@@ -118,7 +124,7 @@ static __device__ void zkz_generic(float2* W, int kp, int pitch, int nz, int Pz,
     }
     int ikz = kz <= Pz / 2 ? kz : Pz - kz;
     float sz = kz <= Pz / 2 ? 1.0f : -1.0f;
-    kmul(Kc + ikz * 6, sy, sz, F[0], F[1], F[2]);
+    kmul<KG>(Kc + ikz * 6, sy, sz, F[0], F[1], F[2]);
     for (int zz = 0; zz < nz; ++zz) {
       float2 w = cconj(__ldg(twz + (kz * zz) % Pz));
       for (int c = 0; c < 3; ++c) out[c][zz] = cadd(out[c][zz], cmul(F[c], w));
@@ -210,7 +216,7 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
     for (int kp = threadIdx.x; kp < Ly; kp += blockDim.x) {
       int ky = R * kp + r;
       const int iky = ky <= Py / 2 ? ky : Py - ky;
-      zkz_single(W, pitch, kp, Kb + (long long)(KS ? kp : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f);
+      zkz_single<!KS>(W, pitch, kp, Kb + (long long)(KS ? kp : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f);
     }
   } else if constexpr (NZ > 1) {
     const int half = blockDim.x >> 1;
@@ -219,14 +225,14 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
       bool valid = kp < Ly;
       int ky = valid ? R * kp + r : r;
       const int iky = ky <= Py / 2 ? ky : Py - ky;
-      zkz_pair<NZ>(W, pitch, valid ? kp : 0, valid, threadIdx.x & 1,
+      zkz_pair<NZ, !KS>(W, pitch, valid ? kp : 0, valid, threadIdx.x & 1,
                    Kb + (long long)(KS ? (valid ? kp : 0) : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f, d.tw_z);
     }
   } else {
     for (int kp = threadIdx.x; kp < Ly; kp += blockDim.x) {
       int ky = R * kp + r;
       const int iky = ky <= Py / 2 ? ky : Py - ky;
-      zkz_generic(W, kp, pitch, nz, g.Pz, Kb + (long long)(KS ? kp : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f,
+      zkz_generic<!KS>(W, kp, pitch, nz, g.Pz, Kb + (long long)(KS ? kp : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f,
                   d.tw_z);
     }
   }

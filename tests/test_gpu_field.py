@@ -86,18 +86,21 @@ def test_large_random_exchange_field_within_bar():
 
 
 def test_radix3_x_length_at_full_tile_capacity():
-    """nx = 1025 pads to Px = 3072 = 3 * 2^10; with ny = 152, nz = 16 the tile
-    holds 8 rows, so pass A/C transform 4 row pairs of 3072 points: 12288
-    values, more than 30 per thread of a 384-thread block (the radix-3 pass
-    holds 10 butterflies of 3 per thread).  Sampled cells against the
-    oracle's direct sum of the demag definition plus its local terms."""
+    """nx = 1025 pads to Px = 3072 = 3 * 2^10, so every x transform ends with
+    a radix-3 pass, which holds a third fewer values per thread than the
+    power-of-two passes (pass A: 15 instead of 16).  With ny = 152, nz = 16
+    the tiles hold 4 rows (pass A's capacity rules out 8), so pass A
+    transforms 2 row pairs of 3072 points: 6144 values, more than 15 per
+    thread of the 384-thread block a 16-value sizing would give.  Sampled
+    cells against the oracle's direct sum of the demag definition plus its
+    local terms."""
     from oracle import demag, fields
     from inputs import Problem
     p = Problem((1025, 152, 16), (3e-9, 3e-9, 2e-9), 1, frozenset({"DEMAG", "EXCH"}))
     p.set("MS", 8e5).set("AEX", 1.3e-11)
     m0 = random_unit_vectors(515, p.shape)
     mag = make_magnet(p, [m0])
-    assert mag.get_shape()["ty"] == 8
+    assert mag.get_shape()["ty"] == 4      # pass A capacity: 4 row pairs of 3072 exceed 15 x 512
     Bg, _ = gpu_eval(mag, p)
     mag.close()
     nx, ny, nz = p.shape
