@@ -248,11 +248,13 @@ int mmp_demag_noalloc(int nx, int ny, int nz, double cx, double cy, double cz, c
  * passes of Methods, Magnetostatic field are laid out on the GPU).
  * --------------------------------------------------------------------- */
 typedef struct mmp_shape {
-    int ty;            /* rows (y) per tile of the x-FFT passes: 2, 4 or 8 */
+    int ty;            /* rows (y) per tile of pass A (stage assembly + forward x FFT): 2, 4 or 8 */
     int radix_x;       /* x FFT plan: 0 = radix-16 passes first, 1 = radix-8 passes */
     int radix_y;       /* plan of the y FFT of pass B (length Py/R), same choices */
     int R;             /* ky residue classes = CTAs per pass-B cluster: 1, 2, 4 or 8 */
     int stage_kernel;  /* 1: pass B stages its slice of the kernel octant in shared memory */
+    int tyc;           /* rows per tile of pass C (inverse x FFT + field): 2, 4, 8, or 0 = the
+                          default (min(ty, 4), fewer when a block cannot hold its row pairs) */
 } mmp_shape;
 
 /* Current shape of the context (chosen at creation: ty from the grid, the

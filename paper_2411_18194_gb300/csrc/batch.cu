@@ -74,7 +74,8 @@ int nz_group(int nz) { return (nz == 1 || nz == 2 || nz == 4 || nz == 8) ? nz : 
 double item_cost(const Grid& g, int pass) {
   auto lg = [](double v) { return v > 1 ? log2(v) : 1.0; };
   if (pass == 1) return 3.0 * g.nz * g.Py * lg(g.Py) + 60.0 * g.Py * g.nz;
-  return (double)g.ty * g.Px * lg(g.Px) + (pass == 2 ? 40.0 * g.ty * g.nx : 0.0);
+  if (pass == 2) return (double)g.tyc * g.Px * lg(g.Px) + 40.0 * g.tyc * g.nx;
+  return (double)g.ty * g.Px * lg(g.Px);
 }
 
 // Block size class of an item: the member's own block size for the pass
@@ -173,6 +174,7 @@ bool eligible(const mmp_ctx* c, const char** why) {
   if (c->method != MMP_DP45) { *why = "batch members use the Dormand-Prince solver"; return false; }
   const Grid& g = c->g;
   if ((long long)g.xb * (g.ty / 2) * g.Px > (long long)fft_cap_a(c->plan_x) * kBatchThreads ||
+      (long long)g.xbc * (g.tyc / 2) * g.Px > (long long)fft_cap_a(c->plan_x) * kBatchThreads ||
       (long long)3 * g.nz * g.Py > 2LL * fft_cap(c->plan_ly) * kBatchThreads) {
     *why = "member tiles or planes exceed the FFT capacity of one batched block";
     return false;
@@ -231,18 +233,18 @@ int build_list(mmp_batch* b, const std::vector<int>& mem) {
   for (int k = 0; k < (int)mem.size(); ++k) {
     const mmp_ctx* c = b->members[mem[k]].ctx;
     const Grid& g = c->g;
-    const int tiles = (g.ny + g.ty - 1) / g.ty;
+    const int tiles = (g.ny + g.ty - 1) / g.ty;       // pass A
+    const int tiles_c = (g.ny + g.tyc - 1) / g.tyc;   // pass C
     const auto ka = std::make_tuple(0, 0, thread_class(c->thrA));
     const auto kb = std::make_tuple(1, nz_group(g.nz), thread_class(c->thrB));
     const auto kc = std::make_tuple(2, 0, thread_class(c->thrC));
     smem[ka] = std::max(smem[ka], smem_a(g));
     smem[kb] = std::max(smem[kb], smem_b(g));
     smem[kc] = std::max(smem[kc], smem_c(g));
-    for (int z = 0; z < g.nz; ++z)
-      for (int t = 0; t < tiles; ++t) {
-        sec[ka].push_back({item_cost(g, 0), BatchItem{k, t, z}});
-        sec[kc].push_back({item_cost(g, 2), BatchItem{k, t, z}});
-      }
+    for (int z = 0; z < g.nz; ++z) {
+      for (int t = 0; t < tiles; ++t) sec[ka].push_back({item_cost(g, 0), BatchItem{k, t, z}});
+      for (int t = 0; t < tiles_c; ++t) sec[kc].push_back({item_cost(g, 2), BatchItem{k, t, z}});
+    }
     for (int kx = 0; kx < g.kxn; ++kx) sec[kb].push_back({item_cost(g, 1), BatchItem{k, kx, 0}});
   }
   std::vector<BatchItem> items;

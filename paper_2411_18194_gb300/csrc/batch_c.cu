@@ -7,7 +7,7 @@
 
 namespace mmp {
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch_field(const BatchInst* __restrict__ insts,
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_field(const BatchInst* __restrict__ insts,
                                                                const BatchItem* __restrict__ items, int stage) {
   extern __shared__ __align__(16) float smem[];
   __shared__ BatchInst si;
@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_field(const BatchInst* 
   const BatchItem w = batch_item(insts, items, si);
   if (threadIdx.x == 0) batch_args(si, stage, sa, fa);
   __syncthreads();
-  field_tile<1, true, true>(smem, si.g, si.d, si.co, fa, w.b, w.a * si.g.ty);
+  field_tile<1, true, true>(smem, si.g, si.d, si.co, fa, w.b, w.a * si.g.tyc);
 }
 
 // Accept the step of every member (fixed-step graphs): flip the ping-pong.

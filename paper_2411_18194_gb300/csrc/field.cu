@@ -11,20 +11,20 @@ namespace cg = cooperative_groups;
 namespace mmp {
 
 template <int NSUB, bool DEMAG, bool UNI>
-__global__ void __launch_bounds__(512) k_field(Grid g, DemagArgs d, Coefs co, FieldArgs f) {
+__global__ void __launch_bounds__(512, 2) k_field(Grid g, DemagArgs d, Coefs co, FieldArgs f) {
   extern __shared__ float smem[];
-  field_tile<NSUB, DEMAG, UNI>(smem, g, d, co, f, blockIdx.y, blockIdx.x * g.ty);
+  field_tile<NSUB, DEMAG, UNI>(smem, g, d, co, f, blockIdx.y, blockIdx.x * g.tyc);
 }
 
 size_t smem_field(const Grid& g, bool demag) {
   if (!demag) return 0;
-  return (size_t)((3 * g.ty * g.nx + 3) & ~3) * sizeof(float) +
-         ((size_t)g.xb * (g.ty >> 1) * fft_pitch(g.Px) + g.Px) * sizeof(float2);
+  return (size_t)((3 * g.tyc * g.nx + 3) & ~3) * sizeof(float) +
+         ((size_t)g.xbc * (g.tyc >> 1) * fft_pitch(g.Px) + g.Px) * sizeof(float2);
 }
 
 cudaError_t launch_field(const Grid& g, const DemagArgs& d, const Coefs& c, const FieldArgs& f, int nsub,
                          bool demag, int threads, cudaStream_t s) {
-  dim3 grid((g.ny + g.ty - 1) / g.ty, g.nz);
+  dim3 grid((g.ny + g.tyc - 1) / g.tyc, g.nz);
   size_t sm = smem_field(g, demag);
   cudaError_t e;
 #define MMP_F(NS, DM, UN)                                               \

@@ -183,6 +183,12 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
   return o;
 }
 
+// Pass C runs two 512-thread blocks per SM (64 registers a thread) on its
+// own tile height (Grid.tyc, 4 rows by default: 100 KB of shared memory on a
+// 2048-point x transform), so its FFT holds 16 values per thread (15 with a
+// radix-3 pass), as pass A's.
+constexpr int kCapC = 16;
+
 // Components c0 .. c0 + nc - 1 of the inverse x transform of pass C:
 // Hermitian-extended row pairs from T (transform (c - c0) np + p), one
 // inverse block_fft, the x < nx outputs into bd[c][row][x].
@@ -191,9 +197,9 @@ __device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbu
   if (nc == 0) return;
   const int nx = g.nx, ny = g.ny, Px = g.Px;
   const int pitch = fft_pitch(Px);
-  const int np = g.ty >> 1;
+  const int np = g.tyc >> 1;
   // groups of FU elements per thread: all loads first, then the stores
-  constexpr int FU = 4;
+  constexpr int FU = 2;
   const int total = nc * np * Px;
   // e / (np Px) by the FP32 quotient of e + 1/2, exact for e < 2^22 (its
   // error (e / d) 2^-23 is below its 1/(2d) distance to an integer); np is
@@ -226,13 +232,13 @@ __device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbu
     }
   }
   __syncthreads();
-  block_fft<true>(fbuf, d.plan_x, nc * np, tw);
-  const float rtn = 1.0f / (float)(g.ty * nx), rnx = 1.0f / (float)nx;   // exact quotients (e < 2^22)
-  for (int e = threadIdx.x; e < nc * g.ty * nx; e += blockDim.x) {
-    const int cc = (int)(((float)e + 0.5f) * rtn), r = e - cc * (g.ty * nx);
+  block_fft<true, kCapC>(fbuf, d.plan_x, nc * np, tw);
+  const float rtn = 1.0f / (float)(g.tyc * nx), rnx = 1.0f / (float)nx;   // exact quotients (e < 2^22)
+  for (int e = threadIdx.x; e < nc * g.tyc * nx; e += blockDim.x) {
+    const int cc = (int)(((float)e + 0.5f) * rtn), r = e - cc * (g.tyc * nx);
     const int row = (int)(((float)r + 0.5f) * rnx), x = r - row * nx;
     float2 v = fbuf[fidx(cc * np + (row >> 1), x, pitch)];
-    bd[((c0 + cc) * g.ty + row) * nx + x] = (row & 1) ? v.y : v.x;
+    bd[((c0 + cc) * g.tyc + row) * nx + x] = (row & 1) ? v.y : v.x;
   }
   __syncthreads();
 }
@@ -244,19 +250,19 @@ __device__ __forceinline__ void field_tile(float* smem, const Grid& g, const Dem
                                            const FieldArgs& f, int z, int y0) {
   const int nx = g.nx, ny = g.ny, Px = g.Px;
   float* bd = smem;                                                     // [3][TY][nx]
-  float2* fbuf = reinterpret_cast<float2*>(smem + ((3 * g.ty * nx + 3) & ~3));   // [NP][Px]
+  float2* fbuf = reinterpret_cast<float2*>(smem + ((3 * g.tyc * nx + 3) & ~3));   // [NP][Px]
   if (DEMAG) {
-    float2* tw = fbuf + g.xb * (g.ty >> 1) * fft_pitch(Px);
+    float2* tw = fbuf + g.xbc * (g.tyc >> 1) * fft_pitch(Px);
     for (int i = threadIdx.x; i < Px; i += blockDim.x) tw[i] = __ldg(d.tw_x + i);
     // straight-line calls, as in pass A; with xb = 3 the first does all three
-    const int rest = g.xb == 3 ? 0 : 1;
-    inverse_x_components(0, g.xb == 3 ? 3 : 1, fbuf, tw, bd, g, d, z, y0);
+    const int rest = g.xbc == 3 ? 0 : 1;
+    inverse_x_components(0, g.xbc == 3 ? 3 : 1, fbuf, tw, bd, g, d, z, y0);
     inverse_x_components(1, rest, fbuf, tw, bd, g, d, z, y0);
     inverse_x_components(2, rest, fbuf, tw, bd, g, d, z, y0);
   }
   float emax = 0.0f, tmax = 0.0f;
   const long long n = g.n;
-  for (int e = threadIdx.x; e < g.ty * nx; e += blockDim.x) {
+  for (int e = threadIdx.x; e < g.tyc * nx; e += blockDim.x) {
     int row = e / nx, x = e - row * nx, y = y0 + row;
     if (y >= ny) continue;
     long long cell = x + (long long)nx * (y + (long long)ny * z);
@@ -264,7 +270,7 @@ __device__ __forceinline__ void field_tile(float* smem, const Grid& g, const Dem
     float b3[3] = {0.0f, 0.0f, 0.0f};
     if (DEMAG) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) b3[c] = bd[(c * g.ty + row) * nx + x];
+      for (int c = 0; c < 3; ++c) b3[c] = bd[(c * g.tyc + row) * nx + x];
     }
 #pragma unroll
     for (int s = 0; s < NSUB; ++s) {

@@ -30,7 +30,9 @@ struct Grid {
   int kyn, kzn;         // Py/2 + 1, Pz/2 + 1
   int krow;             // floats per (kx, ky) row of the kernel octant: 6 kzn rounded up to 4
   int ty;               // rows (y) per tile of passes A and C: 2, 4 or 8 (row pairs = ty / 2)
-  int xb;               // components per x-FFT call of passes A and C: 3 (all at once) or 1
+  int xb;               // components per x-FFT call of pass A: 3 (all at once) or 1
+  int tyc;              // rows (y) per tile of pass C: 2, 4 or 8 (independent of pass A's)
+  int xbc;              // components per x-FFT call of pass C: 3 or 1
   float h[3];           // cell size (m)
   float ih[3];          // 1 / h
 };

@@ -377,6 +377,22 @@ bool shape_ok(const mmp_ctx* ctx, const mmp_shape& s, const char** why) {
     *why = "pass A row pairs above the FFT capacity of a 512-thread block";
     return false;
   }
+  if (s.tyc != 0 && s.tyc != 2 && s.tyc != 4 && s.tyc != 8) { *why = "tyc must be 0, 2, 4 or 8"; return false; }
+  const int tyc = s.tyc ? s.tyc : pick_tile_rows_c(s.ty, g.Px);
+  if ((long long)(tyc / 2) * g.Px > (long long)fft_cap_a(px) * 512) {
+    *why = "pass C row pairs above the FFT capacity of a 512-thread block";
+    return false;
+  }
+  Grid gs = g;   // shared memory of passes A and C at this shape (one component per call)
+  gs.ty = s.ty;
+  gs.xb = 1;
+  gs.tyc = tyc;
+  gs.xbc = 1;
+  if (smem_passA(gs) + (size_t)ctx->nsub * s.ty * g.nx * sizeof(float) > 227 * 1024 ||
+      smem_field(gs, true) > 227 * 1024) {
+    *why = "pass A or C shared memory above 227 KB";
+    return false;
+  }
   if (passb_smem(g.ny, g.nz, g.Py, g.kzn, s.R, s.stage_kernel != 0).total > 227 * 1024) {
     *why = "pass B shared memory above 227 KB";
     return false;
@@ -400,13 +416,16 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
   TRY(upload_table(ctx, ctx->d_tw_x, pass_twiddles(ctx->plan_x)));
   TRY(upload_table(ctx, ctx->d_tw_ly, pass_twiddles(ctx->plan_ly)));
   g.ty = s.ty;
+  g.tyc = s.tyc ? s.tyc : pick_tile_rows_c(s.ty, g.Px);
   // all three components in one x-FFT call when a 512-thread block holds
-  // them and the shared memory of passes A and C fits
+  // them and the pass's shared memory fits (pass A and pass C separately)
   g.xb = 3;
   if ((long long)3 * (g.ty / 2) * g.Px > (long long)fft_cap_a(ctx->plan_x) * 512 ||
-      smem_passA(g) + (size_t)ctx->nsub * g.ty * g.nx * sizeof(float) > 227 * 1024 ||
-      smem_field(g, true) > 227 * 1024)
+      smem_passA(g) + (size_t)ctx->nsub * g.ty * g.nx * sizeof(float) > 227 * 1024)
     g.xb = 1;
+  g.xbc = 3;
+  if ((long long)3 * (g.tyc / 2) * g.Px > (long long)fft_cap_a(ctx->plan_x) * 512 || smem_field(g, true) > 227 * 1024)
+    g.xbc = 1;
   ctx->R = s.R;
   ctx->ks = s.stage_kernel != 0;
   ctx->radix_x = s.radix_x;
@@ -419,6 +438,7 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
 mmp_shape current_shape(const mmp_ctx* ctx) {
   mmp_shape s;
   s.ty = ctx->g.ty;
+  s.tyc = ctx->g.tyc;
   s.radix_x = ctx->radix_x;
   s.radix_y = ctx->radix_y;
   s.R = ctx->R;
@@ -726,6 +746,8 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
   g.krow = (6 * g.kzn + 3) & ~3;
   g.ty = pick_tile_rows(g.ny, g.nz, g.Px);
   g.xb = 1;
+  g.tyc = pick_tile_rows_c(g.ty, g.Px);
+  g.xbc = 1;
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (float)ctx->cell[a];
     g.ih[a] = (float)(1.0 / ctx->cell[a]);
@@ -743,6 +765,7 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
   if (rc == MMP_OK) {
     mmp_shape sh;
     sh.ty = pick_tile_rows(g.ny, g.nz, g.Px);
+    sh.tyc = 0;
     sh.radix_x = 0;
     sh.radix_y = 0;
     sh.R = pick_residues(g);
@@ -1107,13 +1130,15 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
   // pass B (residues, kernel staging, y plan) with A and C as started
   std::vector<mmp_shape> cand_ac, cand_b;
   for (int ty : {2, 4, 8})
-    for (int rx = 0; rx < 2; ++rx) {
-      if (batch && ty != start.ty) continue;   // a batch gets its parallelism from its members
-      mmp_shape s = start;
-      s.ty = ty;
-      s.radix_x = rx;
-      if (shape_ok(ctx, s, &why)) cand_ac.push_back(s);
-    }
+    for (int tyc : {2, 4, 8})
+      for (int rx = 0; rx < 2; ++rx) {
+        if (batch && ty != start.ty) continue;   // a batch gets its parallelism from its members
+        mmp_shape s = start;
+        s.ty = ty;
+        s.tyc = tyc;
+        s.radix_x = rx;
+        if (shape_ok(ctx, s, &why)) cand_ac.push_back(s);
+      }
   for (int R : {1, 2, 4, 8})
     for (int st = 0; st < 2; ++st)
       for (int ry = 0; ry < 2; ++ry) {
@@ -1144,6 +1169,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
     if (t_ac[i] < best_ac) {
       best_ac = t_ac[i];
       best.ty = cand_ac[i].ty;
+      best.tyc = cand_ac[i].tyc;
       best.radix_x = cand_ac[i].radix_x;
     }
   for (size_t i = 0; i < cand_b.size(); ++i)

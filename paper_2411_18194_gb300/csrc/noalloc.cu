@@ -101,6 +101,8 @@ int set_up(Setup& S, int nx, int ny, int nz, const double* cell, cudaStream_t s)
   g.krow = (6 * g.kzn + 3) & ~3;
   g.ty = pick_tile_rows(g.ny, g.nz, g.Px);
   g.xb = 1;
+  g.tyc = pick_tile_rows_c(g.ty, g.Px);
+  g.xbc = 1;
   for (int a = 0; a < 3; ++a) {
     g.h[a] = (float)cell[a];
     g.ih[a] = (float)(1.0 / cell[a]);

@@ -26,6 +26,12 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// wait until at most one (the most recent) group is still in flight
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 
 // 3x3 symmetric kernel times a complex 3-vector.  K points at the six
 // components (xx, yy, zz, xy, xz, yz) of octant entry (|ky|, |kz|); sy, sz
@@ -153,6 +159,19 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
   float* Ks = reinterpret_cast<float*>(sraw + L.ks);
   float2* Tk = d.T + (long long)kx * ncol * ny;
 
+  // 0a. when ny <= Ly the fold has one term: the plane's rows go straight
+  // into the columns, as asynchronous 8-byte copies (all in flight at once,
+  // no registers held); issued before the kernel rows so that waiting for
+  // them leaves the kernel rows in flight
+  const bool one_term = ny <= Ly;
+  if (one_term) {
+    const float rny = 1.0f / (float)ny;   // e / ny by the exact FP32 quotient (e < 2^22)
+    for (int e = threadIdx.x; e < ncol * ny; e += blockDim.x) {
+      const int col = (int)(((float)e + 0.5f) * rny), j = e - col * ny;
+      cp_async8(W + fidx(col, j, pitch), Tk + e);
+    }
+    cp_async_commit();
+  }
   // 0. prefetch this CTA's kernel rows (|ky| of ky = R k' + r) asynchronously
   const int krow = g.krow;
   const float* kbase = d.khat + (long long)kx * g.kyn * krow;
@@ -176,8 +195,26 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
   }
   __syncthreads();
   // 2. fold the ky residue class r: g_r[j] = w^(r j) sum_q T[j + q Ly] w_R^(r q).
-  // Four columns per step keep several independent loads in flight.
-  for (int col0 = 0; col0 < ncol; col0 += 4) {
+  if (one_term) {
+    // rows ny .. Ly-1 of the zero padding, then g_r[j] = w^(r j) T[j]
+    for (int e = threadIdx.x; e < ncol * (Ly - ny); e += blockDim.x) {
+      const int col = e / (Ly - ny), j = ny + e - col * (Ly - ny);
+      W[fidx(col, j, pitch)] = make_float2(0.0f, 0.0f);
+    }
+    if (KS) cp_async_wait_one();
+    else cp_async_wait_all();
+    __syncthreads();
+    if (r > 0) {
+      const float rny = 1.0f / (float)ny;
+      for (int e = threadIdx.x; e < ncol * ny; e += blockDim.x) {
+        const int col = (int)(((float)e + 0.5f) * rny), j = e - col * ny;
+        float2* p = W + fidx(col, j, pitch);
+        *p = cmul(*p, twf[j]);
+      }
+    }
+  }
+  // Otherwise four columns per step keep several independent loads in flight.
+  for (int col0 = 0; col0 < (one_term ? 0 : ncol); col0 += 4) {
     for (int j = threadIdx.x; j < Ly; j += blockDim.x) {
       float2 acc[4];
 #pragma unroll

@@ -94,7 +94,8 @@ inline int fft_cap(int L) {
   FftPlan p;
   return make_plan(L, p) ? fft_cap(p) : 32;
 }
-// Pass A holds half of that (kCapA = 16 values a thread, two blocks per SM).
+// Passes A and C hold half of that (kCapA = kCapC = 16 values a thread, two
+// blocks per SM).
 inline int fft_cap_a(const FftPlan& p) { return fft_cap(p) / 2; }
 inline int fft_cap_a(int L) { return fft_cap(L) / 2; }
 
@@ -124,6 +125,14 @@ inline int pick_residues(const Grid& g) {
 // Rows per tile of passes A and C: 8, or fewer (down to one row pair) while
 // the grid would give fewer than two tiles per SM of the 152, or while pass
 // A's row pairs exceed what a 512-thread block of it holds.
+// Pass C: at most 4 rows (two blocks per SM on the large x lengths), fewer
+// while its row pairs exceed a block's capacity.
+inline int pick_tile_rows_c(int ty, int Px) {
+  int tyc = std::min(ty, 4);
+  while (tyc > 2 && (long long)(tyc / 2) * Px > (long long)fft_cap_a(Px) * 512) tyc >>= 1;
+  return tyc;
+}
+
 inline int pick_tile_rows(int ny, int nz, int Px) {
   int ty = 8;
   while (ty > 2 && (long long)((ny + ty - 1) / ty) * nz < 2 * 152) ty >>= 1;
@@ -137,13 +146,13 @@ inline void launch_threads(const Grid& g, int R, int* thrA, int* thrB, int* thrC
   auto r32 = [](long long v) { return (int)((v + 31) / 32 * 32); };
   auto need = [](long long el, int cap) { return (el + cap - 1) / cap; };
   const int np = g.ty >> 1;
-  const long long fx = need((long long)g.xb * np * g.Px, fft_cap(g.Px));
   const long long fa = need((long long)g.xb * np * g.Px, fft_cap_a(g.Px));
   *thrA = std::min(512, std::max(128, r32(fa)));
   const int Ly = g.Py / R;
   const long long elB = (long long)3 * g.nz * Ly;
   *thrB = std::min(512, std::max(64, r32(std::max(need(elB, fft_cap(Ly)), (long long)Ly))));
-  *thrC = std::min(512, std::max(std::max(128, r32(fx)), r32((long long)g.ty * g.nx / 8)));
+  const long long fc = need((long long)g.xbc * (g.tyc >> 1) * g.Px, fft_cap_a(g.Px));
+  *thrC = std::min(512, std::max(std::max(128, r32(fc)), r32((long long)g.tyc * g.nx / 8)));
 }
 
 }  // namespace mmp
