@@ -26,7 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "field+torque Mcell-evals/s"
-BASELINE_METRIC = "field+torque Mcell-evals/s & served solves/s (p50/p99) vs plain path @ stated err"
+METRIC_FULL = "field+torque Mcell-evals/s & served solves/s (p50/p99) vs plain path @ stated err"
 UNIT = "Mcell-evals/s"
 
 
@@ -99,7 +99,7 @@ class ClockSampler:
 
 
 def kernel_bytes(g, nk_avg, nparts=1, nsub=1, mel=False):
-    """Algorithmic DRAM bytes per launch of each pass (per eval), see the design doc:
+    """Algorithmic DRAM bytes per launch of each pass (per eval):
     each array that a pass must read or write, once."""
     nx, ny, nz = g["shape"]
     n = nx * ny * nz
@@ -209,7 +209,7 @@ def run_reference(args):
     el = time.perf_counter() - t0
     cells = 128 * 128 * 8
     value = (o.evals - e0) * cells / el / 1e6
-    line = {"impl": "reference", "metric": METRIC, "baseline_metric": BASELINE_METRIC, "value": value,
+    line = {"impl": "reference", "metric": METRIC, "metric_full": METRIC_FULL, "value": value,
             "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random m0)",
@@ -278,7 +278,7 @@ def run_serve(args):
     (span,), (solves,) = reduce_over_ranks([st["span_s"]], [st["solves"]], "cuda")
     if rank == 0:
         line = {
-            "metric": "served solves/s", "baseline_metric": BASELINE_METRIC, "value": solves / span,
+            "metric": "served solves/s", "metric_full": METRIC_FULL, "value": solves / span,
             "unit": "solves/s", "n_gpus": ws, "steps": args.requests, "warmup": args.warmup,
             "ms_per_step": span / max(1, st["solves"]) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded arrivals, grids, fields, m0)",
@@ -418,7 +418,7 @@ def run_batch(args):
     nbytes = 12 * sum(cells)
     if rank == 0:
         line = {
-            "metric": METRIC, "baseline_metric": BASELINE_METRIC, "value": value, "unit": UNIT,
+            "metric": METRIC, "metric_full": METRIC_FULL, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded sizes, materials, random m0)",
@@ -574,7 +574,7 @@ def run_gpu(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "baseline_metric": BASELINE_METRIC, "value": value, "unit": UNIT,
+            "metric": METRIC, "metric_full": METRIC_FULL, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random m0)",
