@@ -254,7 +254,7 @@ typedef struct mmp_shape {
     int R;             /* ky residue classes = CTAs per pass-B cluster: 1, 2, 4 or 8 */
     int stage_kernel;  /* 1: pass B stages its slice of the kernel octant in shared memory */
     int tyc;           /* rows per tile of pass C (inverse x FFT + field): 2, 4, 8, or 0 = the
-                          default (min(ty, 4), fewer when a block cannot hold its row pairs) */
+                          default (ty, fewer when a block cannot hold its row pairs) */
 } mmp_shape;
 
 /* Current shape of the context (chosen at creation: ty from the grid, the

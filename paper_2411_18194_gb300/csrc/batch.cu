@@ -174,7 +174,7 @@ bool eligible(const mmp_ctx* c, const char** why) {
   if (c->method != MMP_DP45) { *why = "batch members use the Dormand-Prince solver"; return false; }
   const Grid& g = c->g;
   if ((long long)g.xb * (g.ty / 2) * g.Px > (long long)fft_cap_a(c->plan_x) * kBatchThreads ||
-      (long long)g.xbc * (g.tyc / 2) * g.Px > (long long)fft_cap_a(c->plan_x) * kBatchThreads ||
+      (long long)g.xbc * (g.tyc / 2) * g.Px > (long long)fft_cap(c->plan_x) * kBatchThreads ||
       (long long)3 * g.nz * g.Py > 2LL * fft_cap(c->plan_ly) * kBatchThreads) {
     *why = "member tiles or planes exceed the FFT capacity of one batched block";
     return false;

@@ -7,7 +7,7 @@
 
 namespace mmp {
 
-__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_field(const BatchInst* __restrict__ insts,
+__global__ void __launch_bounds__(kBatchThreads) k_batch_field(const BatchInst* __restrict__ insts,
                                                                const BatchItem* __restrict__ items, int stage) {
   extern __shared__ __align__(16) float smem[];
   __shared__ BatchInst si;

@@ -11,7 +11,7 @@ namespace cg = cooperative_groups;
 namespace mmp {
 
 template <int NSUB, bool DEMAG, bool UNI>
-__global__ void __launch_bounds__(512, 2) k_field(Grid g, DemagArgs d, Coefs co, FieldArgs f) {
+__global__ void __launch_bounds__(512) k_field(Grid g, DemagArgs d, Coefs co, FieldArgs f) {
   extern __shared__ float smem[];
   field_tile<NSUB, DEMAG, UNI>(smem, g, d, co, f, blockIdx.y, blockIdx.x * g.tyc);
 }

@@ -183,11 +183,11 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
   return o;
 }
 
-// Pass C runs two 512-thread blocks per SM (64 registers a thread) on its
-// own tile height (Grid.tyc, 4 rows by default: 100 KB of shared memory on a
-// 2048-point x transform), so its FFT holds 16 values per thread (15 with a
-// radix-3 pass), as pass A's.
-constexpr int kCapC = 16;
+// Pass C has its own tile height (Grid.tyc, tuned with the shape).  Unlike
+// pass A it stays at 128 registers (one 512-thread block per SM): at two
+// blocks of 64 registers it measured no faster (its time goes to the local
+// field arithmetic, not to waiting), so its FFT holds 32 values a thread.
+constexpr int kCapC = 32;
 
 // Components c0 .. c0 + nc - 1 of the inverse x transform of pass C:
 // Hermitian-extended row pairs from T (transform (c - c0) np + p), one
@@ -199,7 +199,7 @@ __device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbu
   const int pitch = fft_pitch(Px);
   const int np = g.tyc >> 1;
   // groups of FU elements per thread: all loads first, then the stores
-  constexpr int FU = 2;
+  constexpr int FU = 4;
   const int total = nc * np * Px;
   // e / (np Px) by the FP32 quotient of e + 1/2, exact for e < 2^22 (its
   // error (e / d) 2^-23 is below its 1/(2d) distance to an integer); np is

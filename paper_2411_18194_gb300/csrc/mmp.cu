@@ -379,7 +379,7 @@ bool shape_ok(const mmp_ctx* ctx, const mmp_shape& s, const char** why) {
   }
   if (s.tyc != 0 && s.tyc != 2 && s.tyc != 4 && s.tyc != 8) { *why = "tyc must be 0, 2, 4 or 8"; return false; }
   const int tyc = s.tyc ? s.tyc : pick_tile_rows_c(s.ty, g.Px);
-  if ((long long)(tyc / 2) * g.Px > (long long)fft_cap_a(px) * 512) {
+  if ((long long)(tyc / 2) * g.Px > (long long)fft_cap(px) * 512) {
     *why = "pass C row pairs above the FFT capacity of a 512-thread block";
     return false;
   }
@@ -424,7 +424,7 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
       smem_passA(g) + (size_t)ctx->nsub * g.ty * g.nx * sizeof(float) > 227 * 1024)
     g.xb = 1;
   g.xbc = 3;
-  if ((long long)3 * (g.tyc / 2) * g.Px > (long long)fft_cap_a(ctx->plan_x) * 512 || smem_field(g, true) > 227 * 1024)
+  if ((long long)3 * (g.tyc / 2) * g.Px > (long long)fft_cap(ctx->plan_x) * 512 || smem_field(g, true) > 227 * 1024)
     g.xbc = 1;
   ctx->R = s.R;
   ctx->ks = s.stage_kernel != 0;

@@ -94,8 +94,7 @@ inline int fft_cap(int L) {
   FftPlan p;
   return make_plan(L, p) ? fft_cap(p) : 32;
 }
-// Passes A and C hold half of that (kCapA = kCapC = 16 values a thread, two
-// blocks per SM).
+// Pass A holds half of that (kCapA = 16 values a thread, two blocks per SM).
 inline int fft_cap_a(const FftPlan& p) { return fft_cap(p) / 2; }
 inline int fft_cap_a(int L) { return fft_cap(L) / 2; }
 
@@ -125,11 +124,11 @@ inline int pick_residues(const Grid& g) {
 // Rows per tile of passes A and C: 8, or fewer (down to one row pair) while
 // the grid would give fewer than two tiles per SM of the 152, or while pass
 // A's row pairs exceed what a 512-thread block of it holds.
-// Pass C: at most 4 rows (two blocks per SM on the large x lengths), fewer
-// while its row pairs exceed a block's capacity.
+// Pass C: pass A's tile height, fewer rows while its row pairs exceed what
+// a 512-thread block of it holds.
 inline int pick_tile_rows_c(int ty, int Px) {
-  int tyc = std::min(ty, 4);
-  while (tyc > 2 && (long long)(tyc / 2) * Px > (long long)fft_cap_a(Px) * 512) tyc >>= 1;
+  int tyc = ty;
+  while (tyc > 2 && (long long)(tyc / 2) * Px > (long long)fft_cap(Px) * 512) tyc >>= 1;
   return tyc;
 }
 
@@ -151,7 +150,7 @@ inline void launch_threads(const Grid& g, int R, int* thrA, int* thrB, int* thrC
   const int Ly = g.Py / R;
   const long long elB = (long long)3 * g.nz * Ly;
   *thrB = std::min(512, std::max(64, r32(std::max(need(elB, fft_cap(Ly)), (long long)Ly))));
-  const long long fc = need((long long)g.xbc * (g.tyc >> 1) * g.Px, fft_cap_a(g.Px));
+  const long long fc = need((long long)g.xbc * (g.tyc >> 1) * g.Px, fft_cap(g.Px));
   *thrC = std::min(512, std::max(std::max(128, r32(fc)), r32((long long)g.tyc * g.nx / 8)));
 }
 
