@@ -153,8 +153,9 @@ int mmp_set_param3(mmp_ctx* ctx, int sub, int param, int region, double x, doubl
 int mmp_set_global(mmp_ctx* ctx, int param, double value);
 
 /* Select the field terms (bitmask of mmp_term).  Two-sublattice contexts
- * with DMI, and the elastic/magnetoelastic terms with empty cells, are
- * rejected (MMP_E_INVAL at the next evaluation). */
+ * with DMI, the magnetoelastic term without the elastic term, and the
+ * elastic/magnetoelastic terms with empty cells are rejected (MMP_E_INVAL
+ * at the next evaluation). */
 int mmp_enable_terms(mmp_ctx* ctx, unsigned terms);
 
 /* State.  m: [3][nz][ny][nx] float32 of sublattice `sub`; with normalize != 0
@@ -196,6 +197,17 @@ int mmp_relax(mmp_ctx* ctx, double torque_tol_T, double max_time, double timeout
  * steps) since creation. */
 int mmp_get_time(mmp_ctx* ctx, double* t, double* dt, long long* steps,
                  long long* rejected, long long* evals);
+
+/* Energy of every field term at the current state, in J:
+ * e_terms[i] for the term with bit (1 << i) of mmp_term (0 for terms that
+ * are off), MMP_NTERMS entries.  Exchange, DMI and the intersublattice
+ * exchange over pairs of neighbouring magnetic cells; demag -1/2 sum M.B dV;
+ * anisotropy, cubic, Zeeman and magnetoelastic densities; elastic strain plus
+ * kinetic energy.  (The fields are minus the gradients of these energies,
+ * Methods, Micromagnetism.)  One extra demag-only evaluation when the demag
+ * term is on (not counted as a solver evaluation).  Synchronises. */
+#define MMP_NTERMS 9
+int mmp_energy(mmp_ctx* ctx, double* e_terms);
 
 /* Checkpoint: serialise (size query with blob = NULL) / restore the state
  * (m of every sublattice, u, v, t, dt, counters) to/from a host blob.  A

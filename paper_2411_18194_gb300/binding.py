@@ -75,6 +75,7 @@ _SIGS = {
     "mmp_profile_read": ([_c.c_void_p, _c.c_int, _c.POINTER(_c.c_longlong), _c.POINTER(_c.c_double)],
                          _c.c_int),
     "mmp_get_shape": ([_c.c_void_p, _c.POINTER(Shape)], _c.c_int),
+    "mmp_energy": ([_c.c_void_p, _c.POINTER(_c.c_double)], _c.c_int),
     "mmp_set_shape": ([_c.c_void_p, _c.POINTER(Shape)], _c.c_int),
     "mmp_autotune": ([_c.c_void_p, _c.c_int, _c.POINTER(Shape), _c.POINTER(_c.c_double)], _c.c_int),
     "mmp_batch_create": ([_c.POINTER(_c.c_void_p), _c.c_void_p], _c.c_int),
@@ -305,6 +306,12 @@ class Magnet:
             if n.value:
                 out[name] = (n.value, ms.value)
         return out
+
+    def energy(self):
+        """{term name: energy (J)} of the enabled terms (mmp_energy)."""
+        buf = (ctypes.c_double * 9)()
+        _check(library().mmp_energy(self._ctx, buf))
+        return {name: buf[bit.bit_length() - 1] for name, bit in TERM_BITS.items()}
 
     # -------------------------------------------------------------- shape --
     def get_shape(self):

@@ -45,6 +45,7 @@ struct mmp_ctx {
   std::tuple<int, int, int, int, double, double, double> khat_key;
   float2 *d_tw_x = nullptr, *d_tw_y = nullptr, *d_tw_ly = nullptr, *d_tw_z = nullptr;
   unsigned* d_red = nullptr;   // [0] error bits, [1] torque bits
+  double* d_energy = nullptr;  // [MMP_NTERMS] (mmp_energy)
   unsigned* h_red = nullptr;   // pinned
   int nparts = 0;              // 3-vectors in the state
   long long nstate = 0;        // floats in the state

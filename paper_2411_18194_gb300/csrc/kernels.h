@@ -92,6 +92,23 @@ struct ElasticArgs {
   unsigned terms;
 };
 
+// Energy of every field term (energy.cu): accumulators out[i] for the term
+// with bit (1 << i), in J.
+struct EnergyArgs {
+  const float* m;          // state: sublattice parts first
+  const float* Bd;         // demag field [nsub][3][n] (DEMAG) or null
+  const float* eps;        // strain [6][n] (MEL, ELASTIC) or null
+  const float* sig;        // stress [6][n] (ELASTIC) or null
+  const float* vel;        // elastic velocity [3][n] (ELASTIC) or null
+  double* out;             // [MMP_NTERMS] accumulators (J)
+  unsigned terms;
+  int nsub;
+  double dV;
+  double a12;              // A12 (J/m)
+  double a0c;              // 4 A0 / a^2 (J/m^3)
+  double rho;
+};
+
 // launchers (return cudaGetLastError())
 cudaError_t launch_assemble(const Grid& g, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_passA(const Grid& g, const StageArgs& a, const DemagArgs& d, const Coefs& c,
@@ -103,6 +120,7 @@ cudaError_t launch_strain(const Grid& g, const ElasticArgs& e, int nsub, cudaStr
 cudaError_t launch_elastic_rhs(const Grid& g, const ElasticArgs& e, const Coefs& c, int nsub,
                                cudaStream_t s);
 cudaError_t launch_normalize(float* m, long long n, cudaStream_t s);
+cudaError_t launch_energy(const Grid& g, const Coefs& co, const EnergyArgs& a, cudaStream_t s);
 
 // Shared-memory carve-up of one pass-B CTA (bytes from the start).
 struct PassBSmem {

@@ -320,6 +320,8 @@ int build_khat(mmp_ctx* ctx) {
 int validate_terms(mmp_ctx* ctx) {
   if (ctx->nsub == 2 && has(ctx, MMP_T_DMI))
     return fail(MMP_E_INVAL, "DMI with two sublattices is not supported (its boundary condition couples them)");
+  if (has(ctx, MMP_T_MEL) && !has(ctx, MMP_T_ELASTIC))
+    return fail(MMP_E_INVAL, "the magnetoelastic term needs the elastic term (its strain comes from u)");
   if (has(ctx, MMP_T_MEL) || has(ctx, MMP_T_ELASTIC)) {
     // empty cells would need free elastic surfaces inside the grid
     for (int s = 0; s < ctx->nsub; ++s)
@@ -790,7 +792,8 @@ int mmp_destroy(mmp_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   release_khat(ctx);
   void* bufs[] = {ctx->d_regions, ctx->d_coef, ctx->d_hA, ctx->d_y, ctx->d_stage, ctx->d_B, ctx->d_eps,
-                  ctx->d_sig, ctx->d_T, ctx->d_tw_x, ctx->d_tw_y, ctx->d_tw_ly, ctx->d_tw_z, ctx->d_red};
+                  ctx->d_sig, ctx->d_T, ctx->d_tw_x, ctx->d_tw_y, ctx->d_tw_ly, ctx->d_tw_z, ctx->d_red,
+                  ctx->d_energy};
   for (void* p : bufs) dfree(ctx, p);
   for (int i = 0; i < 7; ++i) dfree(ctx, ctx->d_k[i]);
   if (ctx->h_red) cudaFreeHost(ctx->h_red);
@@ -1071,6 +1074,61 @@ int mmp_profile_read(mmp_ctx* ctx, int kernel, long long* launches, double* tota
   }
   if (launches) *launches = (long long)ctx->prof_used[kernel];
   if (total_ms) *total_ms = tot;
+  return MMP_OK;
+}
+
+int mmp_energy(mmp_ctx* ctx, double* e_terms) {
+  TRY(check_ctx(ctx));
+  if (!e_terms) return fail(MMP_E_INVAL, "e_terms is null");
+  TRY(prepare(ctx));
+  const long long n = ctx->g.n;
+  if (!ctx->d_energy) TRY(alloc_into(ctx, ctx->d_energy, MMP_NTERMS * sizeof(double)));
+  CK(cudaMemsetAsync(ctx->d_energy, 0, MMP_NTERMS * sizeof(double), ctx->stream), "reset energy");
+  const unsigned terms = ctx->terms;
+  if (terms & MMP_T_DEMAG) {
+    // B_demag of every sublattice: an evaluation with the demag term alone
+    // (torque into the stage buffer, which holds nothing between steps)
+    if (!ctx->d_B) TRY(alloc_into(ctx, ctx->d_B, 3LL * ctx->nsub * n * sizeof(float)));
+    const long long evals = ctx->evals;
+    ctx->terms = MMP_T_DEMAG;
+    StageArgs sa;
+    memset(&sa, 0, sizeof sa);
+    int rc = evaluate(ctx, sa, ctx->d_y, ctx->d_stage, ctx->d_B, nullptr, nullptr, nullptr, 0, nullptr);
+    ctx->terms = terms;
+    ctx->evals = evals;
+    TRY(rc);
+  }
+  const bool strain = (terms & (MMP_T_MEL | MMP_T_ELASTIC)) != 0;
+  if (strain) {
+    ElasticArgs ea;
+    memset(&ea, 0, sizeof ea);
+    ea.stage = ctx->d_y;
+    ea.eps = ctx->d_eps;
+    ea.sig = ctx->d_sig;
+    ea.c11 = (float)ctx->glob[MMP_C11];
+    ea.c12 = (float)ctx->glob[MMP_C12];
+    ea.c44 = (float)ctx->glob[MMP_C44];
+    ea.terms = terms;
+    CK(launch_strain(ctx->g, ea, ctx->nsub, ctx->stream), "strain");
+  }
+  EnergyArgs a;
+  memset(&a, 0, sizeof a);
+  a.m = ctx->d_y;
+  a.Bd = (terms & MMP_T_DEMAG) ? ctx->d_B : nullptr;
+  a.eps = strain ? ctx->d_eps : nullptr;
+  a.sig = (terms & MMP_T_ELASTIC) ? ctx->d_sig : nullptr;
+  a.vel = (terms & MMP_T_ELASTIC) ? ctx->d_y + 3LL * (ctx->nsub + 1) * n : nullptr;
+  a.out = ctx->d_energy;
+  a.terms = terms;
+  a.nsub = ctx->nsub;
+  a.dV = ctx->cell[0] * ctx->cell[1] * ctx->cell[2];
+  a.a12 = ctx->glob[MMP_A12];
+  a.a0c = ctx->glob[MMP_LATTICE_A] > 0 ? 4.0 * ctx->glob[MMP_A0] / (ctx->glob[MMP_LATTICE_A] * ctx->glob[MMP_LATTICE_A]) : 0.0;
+  a.rho = ctx->glob[MMP_RHO];
+  CK(launch_energy(ctx->g, coefs(ctx), a, ctx->stream), "energy");
+  CK(cudaMemcpyAsync(e_terms, ctx->d_energy, MMP_NTERMS * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+     "read energy");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
   return MMP_OK;
 }
 
