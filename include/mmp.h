@@ -180,9 +180,12 @@ int mmp_set_solver(mmp_ctx* ctx, int method, int adaptive, double dt, double tol
  * [3][nz][ny][nx] float32, host or device, either may be NULL. */
 int mmp_eval_field(mmp_ctx* ctx, int sub, float* B, float* tau);
 
-/* Advance nsteps DP45 steps (fixed or adaptive; an adaptive step reads the
- * 4-byte error estimate back once per attempt).  Returns MMP_E_NONFINITE
- * (state rolled back to the last accepted step) if the error is NaN/Inf. */
+/* Advance nsteps steps (fixed or adaptive; an adaptive step reads the
+ * 4-byte error estimate back once per attempt).  Fixed steps run in pairs
+ * from a CUDA graph captured on a private stream (ordered with the
+ * context's stream by events; re-captured after any change it depends on),
+ * bitwise equal to single steps.  Returns MMP_E_NONFINITE (state rolled back
+ * to the last accepted step) if the error is NaN/Inf. */
 int mmp_step(mmp_ctx* ctx, int nsteps);
 
 /* Advance by `duration` seconds (the last step is shortened to land on time). */

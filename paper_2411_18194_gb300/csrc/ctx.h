@@ -61,6 +61,15 @@ struct mmp_ctx {
   long long steps = 0, rejected = 0, evals = 0;
   bool k1_valid = false;
   int k1_relax = 0;
+  // fixed-step graph (replay_pairs): two captured steps and what they assumed
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec = nullptr;
+  float* g_y = nullptr;
+  float* g_k0 = nullptr;
+  double g_dt = 0.0;
+  int g_method = -1, g_ks = 0;
+  long long config_gen = 0, g_config_gen = -1;   // bumped by changes a graph would have baked in
   // tracing
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[MMP_NKERNEL];

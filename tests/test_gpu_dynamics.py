@@ -227,3 +227,31 @@ def test_other_embedded_solvers_match_oracle(method):
     assert abs(info["steps"] - stats["accepted"]) <= max(2, 0.05 * stats["accepted"])
     assert np.abs(_get_m(mag, p) - st.ms[0]).max() <= 1e-4
     mag.close()
+
+
+def test_fixed_step_graph_pairs_are_bitwise_single_steps():
+    """mmp_step(n) with a fixed step replays pairs of steps from a CUDA graph;
+    the result, time and counters equal n single steps, also after the step
+    and the region map change (the graph is captured again)."""
+    w = config_small((20, 14, 2), (2e-9, 2e-9, 1e-9), 171)
+    p = w.problem
+    a = make_magnet(p, w.m0)
+    b = make_magnet(p, w.m0)
+    for mag in (a, b):
+        mag.set_solver(adaptive=False, dt=1e-14)
+    a.step(7)                           # 3 graph pairs + 1 single step
+    for _ in range(7):
+        b.step(1)
+    assert np.array_equal(_get_m(a, p), _get_m(b, p))
+    ta, tb = a.time(), b.time()
+    assert (ta["t"], ta["steps"], ta["evals"]) == (tb["t"], tb["steps"], tb["evals"])
+    for mag in (a, b):
+        mag.set_solver(adaptive=False, dt=7e-15)
+        mag.set_region_map(np.zeros(p.shape[::-1], dtype=np.uint8))
+    a.step(4)
+    for _ in range(4):
+        b.step(1)
+    assert np.array_equal(_get_m(a, p), _get_m(b, p))
+    assert a.time()["evals"] == b.time()["evals"]
+    a.close()
+    b.close()
