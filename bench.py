@@ -620,9 +620,9 @@ def run_gpu(args):
 
 
 def parse_shape(text):
-    """--shape ty,radix_x,radix_y,R,stage_kernel[,tyc[,tb]]"""
+    """--shape ty,radix_x,radix_y,R,stage_kernel[,tyc]"""
     v = [int(x) for x in text.split(",")]
-    return dict(zip(("ty", "radix_x", "radix_y", "R", "stage_kernel", "tyc", "tb"), v))
+    return dict(zip(("ty", "radix_x", "radix_y", "R", "stage_kernel", "tyc"), v))
 
 
 def run_profile_evals(args):
@@ -658,7 +658,7 @@ def main():
                     help="c2 (default, the benchmark line); c1, c3 for the other single workloads; "
                          "c4 the batch of uneven instances; c5 the served request stream")
     ap.add_argument("--instances", type=int, default=256, help="c4: number of instances")
-    ap.add_argument("--shape", default="", help="single workloads: ty,radix_x,radix_y,R,stage_kernel[,tyc[,tb]] "
+    ap.add_argument("--shape", default="", help="single workloads: ty,radix_x,radix_y,R,stage_kernel[,tyc] "
                                                 "instead of the autotuned shape (profiling commands)")
     ap.add_argument("--requests", type=int, default=48, help="c5: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="c5: mean arrival rate (1/s)")

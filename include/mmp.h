@@ -270,14 +270,10 @@ typedef struct mmp_shape {
     int stage_kernel;  /* 1: pass B stages its slice of the kernel octant in shared memory */
     int tyc;           /* rows per tile of pass C (inverse x FFT + field): 2, 4, 8, or 0 = the
                           default (ty, fewer when a block cannot hold its row pairs) */
-    int tb;            /* threads per pass-B block: 128, 256, 512, or 0 = the default (512, fewer
-                          for short planes).  A smaller block of 128 registers a thread lets two
-                          or more clusters share an SM when their shared memory fits, so that
-                          one block's loads overlap another's transforms. */
 } mmp_shape;
 
 /* Current shape of the context (chosen at creation: ty from the grid, the
- * radix-16 plans, the smallest R that fits, stage_kernel = 1, tb = 0). */
+ * radix-16 plans, the smallest R that fits, stage_kernel = 1). */
 int mmp_get_shape(mmp_ctx* ctx, mmp_shape* out);
 
 /* Set a shape.  MMP_E_INVAL (context unchanged) if it does not fit the grid
@@ -291,7 +287,7 @@ int mmp_set_shape(mmp_ctx* ctx, const mmp_shape* shape);
 /* Time the valid shapes on the context's current state and keep the
  * fastest: after a warm-up of ~100 ms of evaluations (loaded clocks), the
  * candidates of passes A+C (tile rows, x plan) and of pass B (R, staging,
- * y plan, block size where a smaller block lets two clusters share an SM) are timed separately in two interleaved rounds (CUDA events per
+ * y plan) are timed separately in two interleaved rounds (CUDA events per
  * pass on the context's stream, the better round counts); the combination
  * replaces the starting shape only if a longer interleaved measurement
  * finds it > 2 % faster per evaluation.  Returns the shape (chosen, may be

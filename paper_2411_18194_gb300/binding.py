@@ -31,8 +31,7 @@ TUNE_BATCH, TUNE_FORCE = 1, 2
 class Shape(ctypes.Structure):
     """mmp_shape: launch shape of the demag passes."""
     _fields_ = [("ty", ctypes.c_int), ("radix_x", ctypes.c_int), ("radix_y", ctypes.c_int),
-                ("R", ctypes.c_int), ("stage_kernel", ctypes.c_int), ("tyc", ctypes.c_int),
-                ("tb", ctypes.c_int)]
+                ("R", ctypes.c_int), ("stage_kernel", ctypes.c_int), ("tyc", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -321,7 +320,7 @@ class Magnet:
         return sh.as_dict()
 
     def set_shape(self, **kw):
-        """Change fields of the launch shape (ty, radix_x, radix_y, R, stage_kernel, tyc, tb)."""
+        """Change fields of the launch shape (ty, radix_x, radix_y, R, stage_kernel, tyc)."""
         d = self.get_shape()
         d.update(kw)
         sh = Shape(**d)

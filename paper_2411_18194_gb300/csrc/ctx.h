@@ -53,7 +53,6 @@ struct mmp_ctx {
   int R = 1, thrA = 256, thrB = 256, thrC = 256;
   int ks = 1;                  // pass B stages the kernel slice in shared memory
   int radix_x = 0, radix_y = 0;   // FFT plan variants (make_plan)
-  int tb = 0;                     // pass-B block size of the shape (0 = launch_threads' choice)
   // solver
   int method = 0;              // MMP_DP45, ... (dp45.h tableau)
   int adaptive = 0;

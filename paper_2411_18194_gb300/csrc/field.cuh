@@ -206,18 +206,13 @@ __device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbu
   // a power of two
   const float rnp = 1.0f / (float)(np * Px);
   const int npsh = __ffs(np) - 1;
-  // element order within a transform: runs of W consecutive k (W the
-  // largest power of two <= 16 dividing Px) for each row pair p, so that a
-  // half-warp stores 16 consecutive words of one row (no bank conflicts)
-  // while the two lanes of a k with p, p+1 still read one 32-byte sector
-  const int wsh = min(4, __ffs(Px) - 1), wm = (1 << wsh) - 1;
   for (int e0 = threadIdx.x; e0 < total; e0 += FU * blockDim.x) {
     float2 va[FU], vb[FU];
 #pragma unroll
     for (int u = 0; u < FU; ++u) {
       const int e = e0 + u * blockDim.x;
       const int cc = (int)(((float)e + 0.5f) * rnp), r = e - cc * (np * Px);
-      const int k = ((r >> (wsh + npsh)) << wsh) | (r & wm), p = (r >> wsh) & (np - 1);
+      const int k = r >> npsh, p = r & (np - 1);
       const int kk = k <= Px / 2 ? k : Px - k;
       const int ya = y0 + 2 * p, yb = ya + 1;
       const float2* Tc = d.T + (((long long)kk * 3 + c0 + cc) * g.nz + z) * ny;
@@ -230,7 +225,7 @@ __device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbu
       const int e = e0 + u * blockDim.x;
       if (e >= total) continue;
       const int cc = (int)(((float)e + 0.5f) * rnp), r = e - cc * (np * Px);
-      const int k = ((r >> (wsh + npsh)) << wsh) | (r & wm), p = (r >> wsh) & (np - 1);
+      const int k = r >> npsh, p = r & (np - 1);
       float2 xa = va[u], xb = vb[u];
       if (k > Px / 2) { xa.y = -xa.y; xb.y = -xb.y; }
       fbuf[fidx(cc * np + p, k, pitch)] = make_float2(xa.x - xb.y, xa.y + xb.x);

@@ -399,22 +399,9 @@ bool shape_ok(const mmp_ctx* ctx, const mmp_shape& s, const char** why) {
     *why = "pass B shared memory above 227 KB";
     return false;
   }
-  if (s.tb != 0 && s.tb != 128 && s.tb != 256 && s.tb != 512) { *why = "tb must be 0, 128, 256 or 512"; return false; }
-  {
-    // the plane's columns in at most two transform calls of the block
-    // (columns per call: fft_cap * threads / Ly, at least one)
-    Grid gb = g;
-    int thrA, thrB, thrC;
-    gb.ty = s.ty;
-    gb.tyc = tyc;
-    gb.xb = gb.xbc = 1;
-    launch_threads(gb, s.R, &thrA, &thrB, &thrC);
-    const long long thr = s.tb ? s.tb : thrB, Ly = g.Py / s.R;
-    const long long per_call = (long long)fft_cap(py) * thr / Ly;
-    if (per_call < 1 || 3LL * g.nz > 2 * per_call) {
-      *why = "pass B plane above two chunks of the FFT capacity of its block";
-      return false;
-    }
+  if ((long long)3 * g.nz * (g.Py / s.R) > 2LL * fft_cap(py) * 512) {
+    *why = "pass B plane above two chunks of the FFT capacity of a 512-thread block";
+    return false;
   }
   return true;
 }
@@ -446,8 +433,6 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
   ctx->radix_x = s.radix_x;
   ctx->radix_y = s.radix_y;
   launch_threads(g, ctx->R, &ctx->thrA, &ctx->thrB, &ctx->thrC);
-  ctx->tb = s.tb;
-  if (s.tb) ctx->thrB = s.tb;
   ctx->k1_valid = false;
   ctx->config_gen++;
   return MMP_OK;
@@ -461,7 +446,6 @@ mmp_shape current_shape(const mmp_ctx* ctx) {
   s.radix_y = ctx->radix_y;
   s.R = ctx->R;
   s.stage_kernel = ctx->ks;
-  s.tb = ctx->tb;
   return s;
 }
 
@@ -853,7 +837,6 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
     sh.radix_y = 0;
     sh.R = pick_residues(g);
     sh.stage_kernel = 1;
-    sh.tb = 0;
     if (sh.R == 0) rc = fail(MMP_E_INVAL, "y-z plane of %d x %d too large for pass B", ny, nz);
     else rc = apply_shape(ctx, sh);
   }
@@ -1262,7 +1245,6 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
   if (batch) {
     start.R = 1;
     start.stage_kernel = 0;
-    start.tb = 0;
     start.ty = 8;   // the largest tiles that fit
     while (start.ty > 2 && !shape_ok(ctx, start, &why)) start.ty >>= 1;
     if (!shape_ok(ctx, start, &why)) return fail(MMP_E_INVAL, "no batch shape fits this grid: %s", why);
@@ -1289,20 +1271,14 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
       }
   for (int R : {1, 2, 4, 8})
     for (int st = 0; st < 2; ++st)
-      for (int ry = 0; ry < 2; ++ry)
-        for (int tb : {0, 128, 256}) {
-          if (batch && (R != 1 || st != 0 || tb != 0)) continue;
-          mmp_shape s = start;
-          s.R = R;
-          s.stage_kernel = st;
-          s.radix_y = ry;
-          s.tb = tb;
-          // a smaller block only pays where it lets more clusters share an SM
-          if (tb && (size_t)(passb_smem(ctx->g.ny, ctx->g.nz, ctx->g.Py, ctx->g.kzn, R, st != 0).total + 1024) * 2 >
-                        228 * 1024)
-            continue;
-          if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
-        }
+      for (int ry = 0; ry < 2; ++ry) {
+        if (batch && (R != 1 || st != 0)) continue;
+        mmp_shape s = start;
+        s.R = R;
+        s.stage_kernel = st;
+        s.radix_y = ry;
+        if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
+      }
   // two interleaved rounds; a candidate's time is its better round
   std::vector<double> t_ac(cand_ac.size(), 1e300), t_b(cand_b.size(), 1e300);
   for (int round = 0; round < 2; ++round) {
@@ -1332,7 +1308,6 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
       best.R = cand_b[i].R;
       best.stage_kernel = cand_b[i].stage_kernel;
       best.radix_y = cand_b[i].radix_y;
-      best.tb = cand_b[i].tb;
     }
   // keep the starting shape unless the combination measures faster by > 2 %
   // (longer, interleaved measurement of both)

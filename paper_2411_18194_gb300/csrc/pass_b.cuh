@@ -66,13 +66,11 @@ __device__ __forceinline__ void zkz_single(float2* W, int pitch, int kp, const f
   W[fidx(0, kp, pitch)] = a; W[fidx(1, kp, pitch)] = b; W[fidx(2, kp, pitch)] = c;
 }
 
-// nz = NZ in {2, 4, 8} (Pz = 2 NZ): two lanes per ky column, lanes l and
-// l + 16 of a warp; the lane's half `par` handles kz of that parity:
-// F[2q+par] = DFT_NZ(v[z] w^(par z))[q], multiply, inverse DFT_NZ, times
-// w^(-par z); the two lanes add their halves through a shuffle and each
-// writes NZ/2 of the z outputs (a half-warp writes 16 consecutive columns of
-// one row: no bank conflicts).  Both lanes read the column before the
-// shuffle, so neither writes before the other read.
+// nz = NZ in {2, 4, 8} (Pz = 2 NZ): two lanes per ky column, lane parity
+// `par` handles kz of that parity:  F[2q+par] = DFT_NZ(v[z] w^(par z))[q],
+// multiply, inverse DFT_NZ, times w^(-par z); the two lanes add their halves
+// through a shuffle and each writes NZ/2 of the z outputs.  Both lanes read
+// the column before the shuffle, so neither writes before the other read.
 template <int NZ, bool KG>
 __device__ __forceinline__ void zkz_pair(float2* W, int pitch, int kp, bool valid, int par, const float* Kc,
                                          float sy, const float2* __restrict__ twz) {
@@ -109,8 +107,8 @@ __device__ __forceinline__ void zkz_pair(float2* W, int pitch, int kp, bool vali
       float2 send = par ? f[c][z] : f[c][z + H];
       float2 keep = par ? f[c][z + H] : f[c][z];
       float2 recv;
-      recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
-      recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+      recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+      recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
       if (valid) W[fidx(c * NZ + z + (par ? H : 0), kp, pitch)] = cadd(keep, recv);
     }
 }
@@ -260,11 +258,11 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
   } else if constexpr (NZ > 1) {
     const int half = blockDim.x >> 1;
     for (int base = 0; base < Ly; base += half) {
-      int kp = base + ((threadIdx.x >> 5) << 4) + (threadIdx.x & 15);
+      int kp = base + (threadIdx.x >> 1);
       bool valid = kp < Ly;
       int ky = valid ? R * kp + r : r;
       const int iky = ky <= Py / 2 ? ky : Py - ky;
-      zkz_pair<NZ, !KS>(W, pitch, valid ? kp : 0, valid, (threadIdx.x >> 4) & 1,
+      zkz_pair<NZ, !KS>(W, pitch, valid ? kp : 0, valid, threadIdx.x & 1,
                    Kb + (long long)(KS ? (valid ? kp : 0) : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f, d.tw_z);
     }
   } else {
