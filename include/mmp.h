@@ -104,7 +104,8 @@ enum mmp_term {
     MMP_T_DEMAG = 1,     /* FFT demag of M = sum_s Ms m (Methods, Magnetostatic field) */
     MMP_T_EXCH = 2,      /* 6-neighbour exchange (first term of Eq. AFM_exchange_field) */
     MMP_T_ANIS = 4,      /* uniaxial anisotropy (KU1, KU2 along ANIS_U; KB1 along ANIS_UB) */
-    MMP_T_DMI = 8,       /* interfacial DMI (Eq. dmi, interfacial tensor) + Neumann BC */
+    MMP_T_DMI = 8,       /* interfacial DMI (Eq. dmi, interfacial tensor) with the boundary
+                            condition of mmp_set_boundary */
     MMP_T_ZEEMAN = 16,   /* external field B_EXT */
     MMP_T_AFM = 32,      /* A12 and A0 terms of Eq. AFM_exchange_field (2 sublattices) */
     MMP_T_MEL = 64,      /* magnetoelastic field/force (Eqs. magnetoelastic-field/-force) */
@@ -112,6 +113,18 @@ enum mmp_term {
     MMP_T_CUBIC = 256    /* cubic anisotropy: energy Kc1 (a^2 b^2 + a^2 c^2 + b^2 c^2), a, b, c the
                             components of m on the cubic axes (the paper's "uniaxial or cubic"
                             anisotropy, as in mumax3) */
+};
+
+/* Boundary condition of the exchange and DMI stencils at the magnet's surface
+ * (grid edges and faces towards empty cells); Methods, DMI and boundary
+ * conditions, which names Neumann (default), open and periodic conditions. */
+enum mmp_bc {
+    MMP_BC_NEUMANN = 0,  /* a missing neighbour takes the ghost value m + Delta_n d_n m with
+                            d_n m = -(D/2A)(z x n) x m (Eq. AFM_Neumann_BC, A12 = 0); zero-Neumann
+                            without DMI */
+    MMP_BC_OPEN = 1      /* a missing neighbour drops out of the exchange and DMI sums (no
+                            boundary twist): the field is the exact negative gradient of the
+                            pair energy.  Without DMI it equals the Neumann field. */
 };
 
 /* Embedded Runge-Kutta solvers of the paper's table (Methods): convergence
@@ -151,6 +164,10 @@ int mmp_set_region_map(mmp_ctx* ctx, const uint8_t* regions);
 int mmp_set_param(mmp_ctx* ctx, int sub, int param, int region, double value);
 int mmp_set_param3(mmp_ctx* ctx, int sub, int param, int region, double x, double y, double z);
 int mmp_set_global(mmp_ctx* ctx, int param, double value);
+
+/* Select the boundary condition (mmp_bc; default MMP_BC_NEUMANN).  Periodic
+ * conditions are not supported (MMP_E_INVAL). */
+int mmp_set_boundary(mmp_ctx* ctx, int bc);
 
 /* Select the field terms (bitmask of mmp_term).  Two-sublattice contexts
  * with DMI, the magnetoelastic term without the elastic term, and the

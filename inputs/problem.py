@@ -35,6 +35,7 @@ class Problem:
     scal: dict = field(default_factory=dict)   # name -> float64 [n_sub][256]
     vec: dict = field(default_factory=dict)    # name -> float64 [n_sub][256][3]
     glob: dict = field(default_factory=dict)   # name -> float
+    open_bc: bool = False             # open boundary (missing neighbours drop out) instead of Neumann
 
     def __post_init__(self):
         for k in PARAM_SCALARS:

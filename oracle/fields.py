@@ -23,6 +23,10 @@ Passages followed (arXiv 2411.18194, Methods):
     interfacial tensor: d_n m = -(D / 2A) (z x n) x m; a missing neighbour
     takes the ghost value m + Delta_n d_n m in the exchange and DMI stencils.
     For two sublattices without DMI the condition reduces to d_n m = 0.
+  * Open boundary (the alternative the same passage names, Problem.open_bc):
+    a missing neighbour drops out of the exchange and DMI sums, so the field
+    is the exact negative gradient of the pair energy (energies()).  Without
+    DMI this equals the Neumann field (the ghost is m).
   * Uniaxial anisotropy "as in mumax3":
         B = (2 Ku1/Ms)(m.u) u + (4 Ku2/Ms)(m.u)^3 u,
     plus a second uniaxial term (2 Kb1/Ms)(m.ub) ub (used for the biaxial
@@ -114,7 +118,8 @@ def ghost_derivative(m, A, D, spatial, d):
 
 def neighbour(p, P, s, m, axis, spatial, d):
     """Neighbour value of sublattice s along (axis, d): the real neighbour if it
-    exists and is magnetic, else the boundary ghost.  Returns
+    exists and is magnetic, else the boundary ghost (Neumann) or, for an open
+    boundary, the cell's own value with D_pair = 0.  Returns
     (value, present mask, A_pair, D_pair)."""
     Ms, A, D = P["MS"][s], P["AEX"][s], P["DIND"][s]
     h = p.cell[spatial]
@@ -124,11 +129,17 @@ def neighbour(p, P, s, m, axis, spatial, d):
     D_nb, _ = shift(D, axis, d)
     present = inside & (Ms_nb > 0)
     use_dmi = "DMI" in p.terms
-    Dg = D if use_dmi else np.zeros_like(D)
-    ghost = m + h * ghost_derivative(m, A, Dg, spatial, d)
-    value = np.where(present, m_nb, ghost)
+    if getattr(p, "open_bc", False):
+        # open: no ghost; the missing pair contributes m - m = 0 to the
+        # exchange sum and carries D = 0 in the DMI sum
+        value = np.where(present, m_nb, m)
+        D_pair = np.where(present, 0.5 * (D + D_nb), 0.0)
+    else:
+        Dg = D if use_dmi else np.zeros_like(D)
+        ghost = m + h * ghost_derivative(m, A, Dg, spatial, d)
+        value = np.where(present, m_nb, ghost)
+        D_pair = np.where(present, 0.5 * (D + D_nb), D)
     A_pair = np.where(present, _harmonic(A, A_nb), A)
-    D_pair = np.where(present, 0.5 * (D + D_nb), D)
     return value, present, A_pair, D_pair
 
 

@@ -26,6 +26,7 @@ STATUS = {0: "MMP_OK", -1: "MMP_E_INVAL", -2: "MMP_E_OOM", -3: "MMP_E_CUDA", -4:
 GOALS = {"steps": 0, "run": 1, "relax": 2}
 METHODS = {"DP45": 0, "HEUN": 1, "BS23": 2, "CASHKARP": 3, "RKF45": 4}
 TUNE_BATCH, TUNE_FORCE = 1, 2
+BOUNDARIES = {"neumann": 0, "open": 1}
 
 
 class Shape(ctypes.Structure):
@@ -53,6 +54,7 @@ _SIGS = {
                         _c.c_double], _c.c_int),
     "mmp_set_global": ([_c.c_void_p, _c.c_int, _c.c_double], _c.c_int),
     "mmp_enable_terms": ([_c.c_void_p, _c.c_uint], _c.c_int),
+    "mmp_set_boundary": ([_c.c_void_p, _c.c_int], _c.c_int),
     "mmp_set_m": ([_c.c_void_p, _c.c_int, _c.c_void_p, _c.c_int], _c.c_int),
     "mmp_get_m": ([_c.c_void_p, _c.c_int, _c.c_void_p], _c.c_int),
     "mmp_set_elastic": ([_c.c_void_p, _c.c_void_p, _c.c_void_p], _c.c_int),
@@ -236,6 +238,10 @@ class Magnet:
     def set_global(self, name, value):
         _check(library().mmp_set_global(self._ctx, GLOBAL_IDS[name], float(value)))
 
+    def set_boundary(self, bc):
+        """Boundary condition of the exchange and DMI stencils: "neumann" or "open"."""
+        _check(library().mmp_set_boundary(self._ctx, BOUNDARIES[bc]))
+
     def enable_terms(self, terms):
         mask = terms if isinstance(terms, int) else sum(TERM_BITS[t] for t in terms)
         _check(library().mmp_enable_terms(self._ctx, mask))
@@ -338,7 +344,8 @@ class Magnet:
     @classmethod
     def from_problem(cls, problem, **kw):
         """A context set up from an object with the attributes of
-        inputs.Problem (shape, cell, n_sub, regions, scal, vec, glob, terms)."""
+        inputs.Problem (shape, cell, n_sub, regions, scal, vec, glob, terms,
+        open_bc)."""
         mag = cls(problem.shape, problem.cell, problem.n_sub, **kw)
         regions = np.ascontiguousarray(problem.regions, dtype=np.uint8)
         used = np.unique(regions)
@@ -365,6 +372,8 @@ class Magnet:
         for name in GLOBAL_IDS:
             mag.set_global(name, problem.glob.get(name, 0.0))
         mag.enable_terms(sorted(problem.terms))
+        if getattr(problem, "open_bc", False):
+            mag.set_boundary("open")
         return mag
 
 

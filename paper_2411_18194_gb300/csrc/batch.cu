@@ -214,7 +214,7 @@ BatchInst make_inst(const Member& m, unsigned* red, double h, int relax) {
   I.kbuf[1] = c->d_k[6];
   for (int j = 0; j < 5; ++j) I.kmid[j] = c->d_k[j + 1];
   I.red = red;
-  I.terms = c->terms;
+  I.terms = kernel_terms(c);
   I.relax = relax;
   I.par = m.par;
   for (int i = 1; i <= 6; ++i) stage_coefs(h, i, I.coef[i]);

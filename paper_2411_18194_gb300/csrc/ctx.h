@@ -23,6 +23,7 @@ struct mmp_ctx {
   void* uuser = nullptr;
   bool poisoned = false;
   unsigned terms = 0;
+  int bc = MMP_BC_NEUMANN;        // boundary condition of the exchange and DMI stencils
   // parameter tables (FP64)
   double scal[MMP_NPARAM][2][MMP_MAX_REGIONS];
   double vec[MMP_NPARAM3][2][MMP_MAX_REGIONS][3];
@@ -75,6 +76,11 @@ struct mmp_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[MMP_NKERNEL];
   size_t prof_used[MMP_NKERNEL] = {};
 };
+
+// Term word of the field kernels: the enabled terms plus the boundary bit.
+inline unsigned kernel_terms(const mmp_ctx* c) {
+  return c->terms | (c->bc == MMP_BC_OPEN ? mmp::kTermOpenBC : 0u);
+}
 
 namespace mmp {
 // Allocate the state, upload coefficients, build the demag kernel spectrum

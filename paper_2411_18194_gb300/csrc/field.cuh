@@ -58,7 +58,7 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
   }
   const float m[3] = {ms[cell], ms[n + cell], ms[2 * n + cell]};
   const unsigned terms = f.terms;
-  const bool EX = terms & 2u, DM = terms & 8u;
+  const bool EX = terms & 2u, DM = terms & 8u, OPEN = terms & kTermOpenBC;
   df acc[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
   float sm[3] = {bd[0], bd[1], bd[2]};
   float dmi[3] = {0.0f, 0.0f, 0.0f};
@@ -94,7 +94,7 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
         if (DM && a < 2)
           dpair = UNI ? R.dmi[a]
                       : 0.5f * (R.dind + co.reg[s * MMP_MAX_REGIONS + rn].dind) * R.inv_ms * g.ih[a];
-      } else if (DM && a < 2) {
+      } else if (DM && a < 2 && !OPEN) {
         // boundary ghost m + h d_n m, d_n m = -(D/2A) (z x n) x m = -(D/2A) d w
         float w[3];
         if (a == 0) { w[0] = m[2]; w[1] = 0.0f; w[2] = -m[0]; }
@@ -109,6 +109,8 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
         }
         dpair = R.dmi[a];
       } else {
+        // no DMI (the ghost is m: zero-Neumann) or an open boundary (dpair
+        // stays 0: the missing pair adds nothing)
         v[0] = m[0]; v[1] = m[1]; v[2] = m[2];
       }
       if (DM && a < 2) {

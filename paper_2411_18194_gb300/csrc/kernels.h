@@ -69,12 +69,16 @@ struct Coefs {
   int uniform;
 };
 
+// Bit of the kernels' term word (above the public mmp_term bits): open
+// boundary, a missing neighbour drops out of the exchange and DMI sums.
+constexpr unsigned kTermOpenBC = 1u << 16;
+
 struct FieldArgs {
   const float* stage;        // stage state
   float* kout;               // output derivative (same layout as the state)
   float* Bout;               // optional B_eff [nsub][3][n]
   const float* eps;          // strain [6][n] (magnetoelastic)
-  unsigned terms;
+  unsigned terms;            // mmp_term bits | kTermOpenBC
   // error estimate of the 5th-order stage: err = max |sum_j e_j k_j|
   const float* ek[6];
   float ecoef[7];            // dt * (b_j - b*_j)

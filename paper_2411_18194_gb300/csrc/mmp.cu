@@ -535,7 +535,7 @@ int evaluate(mmp_ctx* ctx, StageArgs sa, const float* src, float* kout, float* B
   f.kout = kout;
   f.Bout = Bout;
   f.eps = ctx->d_eps;
-  f.terms = ctx->terms;
+  f.terms = kernel_terms(ctx);
   f.err = err;
   if (err) {
     for (int j = 0; j < 7; ++j) f.ecoef[j] = ecoef[j];
@@ -938,6 +938,15 @@ int mmp_set_global(mmp_ctx* ctx, int param, double value) {
   if (!std::isfinite(value)) return fail(MMP_E_INVAL, "non-finite value");
   ctx->glob[param] = value;
   ctx->coef_dirty = true;
+  ctx->k1_valid = false;
+  ctx->config_gen++;
+  return MMP_OK;
+}
+
+int mmp_set_boundary(mmp_ctx* ctx, int bc) {
+  TRY(check_ctx(ctx));
+  if (bc != MMP_BC_NEUMANN && bc != MMP_BC_OPEN) return fail(MMP_E_INVAL, "unsupported boundary condition %d", bc);
+  ctx->bc = bc;
   ctx->k1_valid = false;
   ctx->config_gen++;
   return MMP_OK;

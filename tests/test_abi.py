@@ -32,7 +32,7 @@ def _lib():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("mmp_create", "mmp_destroy", "mmp_set_region_map", "mmp_set_param", "mmp_set_param3",
-              "mmp_set_global", "mmp_enable_terms", "mmp_set_m", "mmp_get_m", "mmp_set_solver",
+              "mmp_set_global", "mmp_enable_terms", "mmp_set_boundary", "mmp_set_m", "mmp_get_m", "mmp_set_solver",
               "mmp_eval_field", "mmp_step", "mmp_run", "mmp_relax", "mmp_get_time", "mmp_get_state",
               "mmp_set_state", "mmp_last_error"):
         assert n in names
@@ -67,6 +67,8 @@ def test_binding_ids_match_header_enums():
         assert enums["MMP_" + name] == v
     for name, v in binding.GOALS.items():
         assert enums["MMP_GOAL_" + name.upper()] == v
+    for name, v in binding.BOUNDARIES.items():
+        assert enums["MMP_BC_" + name.upper()] == v
 
 
 def test_create_rejects_bad_arguments_before_touching_the_device():

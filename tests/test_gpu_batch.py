@@ -174,3 +174,28 @@ def test_autotune_keeps_results_within_tolerance():
     shape2, _ = mag.autotune()
     assert mag.get_shape() == shape2
     mag.close()
+
+
+def test_open_boundary_member_bitwise_equal_to_solo():
+    """A member with DMI and the open boundary carries its boundary into the
+    batched kernels: bitwise equal to its solo run, and different from the
+    same member with the Neumann boundary."""
+    import paper_2411_18194_gb300 as pkg
+    terms = ("DEMAG", "EXCH", "DMI", "ZEEMAN")
+    runs = []
+    for bc in ("open", "open", "neumann"):
+        p, m0, mag = _magnet(2, (48, 32, 2), terms)
+        mag.set_param("DIND", 2e-3)
+        mag.set_boundary(bc)
+        mag.set_solver(adaptive=False, dt=_dt(p))
+        runs.append(mag)
+    batched, solo, neumann = runs
+    with pkg.Batch() as b:
+        b.add(batched, "steps", 10)
+        b.add(neumann, "steps", 10)
+        assert b.advance() == 0
+    solo.step(10)
+    assert np.array_equal(_m(batched), _m(solo))
+    assert not np.array_equal(_m(batched), _m(neumann))
+    for x in runs:
+        x.close()

@@ -188,3 +188,23 @@ def test_every_launch_shape_matches_oracle():
         assert np.all(np.abs(Tg[0] - To[0]) <= tolT), (R, st, ry, ty, tyc)
     assert set(seen) == {1, 2, 4, 8}
     mag.close()
+
+
+def test_open_boundary_parity():
+    """Open boundary (missing neighbours drop out of the exchange and DMI
+    sums) with DMI, several regions and empty cells; the Neumann field of
+    the same state differs at the boundary, so the switch is live."""
+    w = config_small((24, 20, 2), (3e-9, 2e-9, 1e-9), 23, terms=FM, n_regions=3, empty_fraction=0.1)
+    p = w.problem
+    p.open_bc = True
+    mag = make_magnet(p, w.m0)
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0)
+    tolB = field_tolerance(p, Bo[0])
+    assert np.all(np.abs(Bg[0] - Bo[0]) <= tolB), np.abs(Bg[0] - Bo[0]).max()
+    tolT = torque_tolerance(p, Bo[0], tolB)
+    assert np.all(np.abs(Tg[0] - To[0]) <= tolT), np.abs(Tg[0] - To[0]).max()
+    mag.set_boundary("neumann")
+    Bn, _ = gpu_eval(mag, p)
+    assert np.abs(Bn[0] - Bg[0]).max() > 100 * tolB.max()
+    mag.close()

@@ -282,3 +282,84 @@ def test_cubic_anisotropy_closed_forms():
     B = fields.cubic_anisotropy_field(p, P, 0, m)
     assert np.abs(B[:, 0, 0, 0]).max() < 1e-12
     assert np.allclose(B[:, 0, 0, 1], -(4.0 * K / (3.0 * Ms)) * diag, rtol=1e-12, atol=0)
+
+
+def _open_problem(seed, terms=("EXCH", "DMI"), empty=0.2):
+    w = config_small((5, 4, 2), (2e-9, 2.5e-9, 1e-9), seed, terms=terms, n_regions=2, empty_fraction=empty)
+    w.problem.open_bc = True
+    return w
+
+
+@pytest.mark.parametrize("term", ["exch", "dmi"])
+def test_open_boundary_field_is_energy_gradient_everywhere(term):
+    """With the open boundary a missing neighbour drops out of the pair sums,
+    so at every magnetic cell -- corners, edges and faces towards empty cells
+    included -- the field is the negative gradient of the pair energy."""
+    w = _open_problem(31)
+    p = w.problem
+    P = fields.cell_params(p)
+    ms = [w.m0[0].astype(np.float64)]
+    _, parts = fields.effective_fields(p, ms, P=P, parts=True)
+    dV = np.prod(p.cell)
+
+    def E(mm):
+        return fields.energies(p, mm, P=P)[term]
+
+    nx, ny, nz = p.shape
+    checked = 0
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                idx = (z, y, x)
+                if P["MS"][0][idx] == 0:
+                    continue
+                ref = _fd_field(E, ms, 0, idx, P["MS"][0][idx], dV)
+                got = parts[0][term][(slice(None),) + idx]
+                assert np.abs(got - ref).max() <= 1e-6 * max(np.abs(ref).max(), 1e-3), (idx, got, ref)
+                checked += 1
+    assert checked >= 25
+
+
+def test_open_boundary_two_cell_wire_closed_form():
+    """Two cells along x (or y), open ends: each cell sees only the other,
+    B_exch = (2A/Ms)(m' - m)/h^2 and B_dmi = (D/(Ms h)) s (m'_z e_a - m'_a e_z)
+    with s = +1 for the neighbour at +h, -1 at -h."""
+    A, D, Ms, h = 1.5e-11, 3e-3, 8e5, 1e-9
+    for axis in (0, 1):
+        p = _wire(2, axis, D=D, A=A, Ms=Ms, h=h)
+        p.open_bc = True
+        rng = np.random.default_rng(7 + axis)
+        m = rng.normal(size=(3, 2))
+        m /= np.linalg.norm(m, axis=0)
+        shape = [1, 1, 1]
+        shape[axis] = 2
+        ms = [m.reshape((3,) + tuple(shape[::-1]))]
+        _, parts = fields.effective_fields(p, ms, parts=True)
+        ex = parts[0]["exch"].reshape(3, 2)
+        dm = parts[0]["dmi"].reshape(3, 2)
+        for c, s in ((0, 1), (1, -1)):
+            o = 1 - c
+            assert np.allclose(ex[:, c], 2 * A / Ms * (m[:, o] - m[:, c]) / h ** 2, rtol=1e-13)
+            want = np.zeros(3)
+            want[axis] = s * D * m[2, o] / (Ms * h)
+            want[2] = -s * D * m[axis, o] / (Ms * h)
+            assert np.allclose(dm[:, c], want, rtol=1e-13, atol=1e-12)
+
+
+def test_open_and_neumann_boundaries():
+    """Without DMI the two conditions give the same field everywhere; with
+    DMI they agree away from the boundary and differ at x/y boundary cells."""
+    for terms, same in ((("EXCH",), True), (("EXCH", "DMI"), False)):
+        w = config_small((6, 5, 2), (2e-9, 2e-9, 1e-9), 41, terms=terms)
+        p = w.problem
+        ms = [w.m0[0].astype(np.float64)]
+        Bn = fields.effective_fields(p, ms)[0]
+        p.open_bc = True
+        Bo = fields.effective_fields(p, ms)[0]
+        if same:
+            assert np.array_equal(Bn, Bo)
+        else:
+            inner = (slice(None), slice(None), slice(1, -1), slice(1, -1))
+            assert np.allclose(Bn[inner], Bo[inner], rtol=1e-14, atol=0)
+            edge = np.abs(Bn - Bo).max(axis=0)
+            assert edge[:, 0, :].min() > 0 and edge[:, :, 0].min() > 0
