@@ -120,6 +120,30 @@ def kernel_bytes(g, nk_avg, nparts=1, nsub=1, mel=False):
     }
 
 
+def eval_flops(g, nsub=1):
+    """Algorithmic FP32 flops of one field evaluation (the FFT counted as
+    5 N log2 N per complex transform of length N): the forward x transform
+    of real row pairs (pass A), the y transforms both ways, the z transforms
+    both ways and the 3x3 multiply (36 flops per frequency, pass B), the
+    inverse x transform (pass C) and ~150 flops of local field and torque per
+    cell and sublattice."""
+    import math
+    nx, ny, nz = g["shape"]
+    Px, Py, Pz = g["Px"], g["Py"], g["Pz"]
+    kxn = Px // 2 + 1
+
+    def fft(n):
+        return 5.0 * n * math.log2(n) if n > 1 else 0.0
+    x = 3 * nz * ((ny + 1) // 2) * fft(Px)
+    y = 2 * 3 * nz * kxn * fft(Py)
+    z = 2 * 3 * kxn * Py * fft(Pz)
+    mult = 36.0 * kxn * Py * Pz
+    return 2 * x + y + z + mult + 150.0 * nx * ny * nz * nsub
+
+
+FLOOR_BYTES = 99   # compulsory DRAM bytes per cell-eval of the large ferromagnet (m, k, kernel, one spectrum round trip)
+
+
 def geometry(shape):
     def nice(n):
         if n == 1:
@@ -609,6 +633,19 @@ def run_gpu(args):
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clk,
+        }
+        # path-level figures: effective algorithmic bandwidth (the passes'
+        # bytes, and the compulsory floor) and achieved FP32 rate
+        cell_evals = nx * ny * nz * p.n_sub
+        per_eval_bytes = sum(kb.values())
+        rate = value * 1e6 / cell_evals                 # evaluations per second
+        line["path"] = {
+            "algorithmic_bytes_per_cell_eval": round(per_eval_bytes / cell_evals, 1),
+            "algorithmic_gbs": round(rate * per_eval_bytes / 1e9, 1),
+            "floor_bytes_per_cell_eval": FLOOR_BYTES,
+            "floor_gbs": round(value * 1e6 * FLOOR_BYTES / 1e9, 1),
+            "fp32_gflop_per_eval": round(eval_flops(g, p.n_sub) / 1e9, 3),
+            "fp32_gflops": round(rate * eval_flops(g, p.n_sub) / 1e9, 1),
         }
         if graph_path:
             line["graph_path"] = graph_path
