@@ -134,3 +134,14 @@ int main() {
             m = ids[int(f[0])]
             assert int(f[1]) == METHODS[m]["S"] and float(f[2]) == METHODS[m]["exponent"]
     assert seen > 50
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built library every entry point raises."""
+    from paper_2411_18194_gb300 import binding
+    monkeypatch.setattr(binding, "_LIB_PATH", str(tmp_path / "libmmp.so"))
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(RuntimeError, match="libmmp.so not found"):
+        binding.library()
+    with pytest.raises(RuntimeError, match="libmmp.so not found"):
+        binding.Magnet((4, 4, 1), (1e-9, 1e-9, 1e-9), 1)
