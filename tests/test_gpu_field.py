@@ -2,9 +2,10 @@
 C-ABI) with the FP64 oracle, element by element, on seeded inputs.
 
 Sizes span several x/y tiles with ragged tails, padded lengths 2^k and
-3*2^k, the pass-B cluster split of large ky planes (R = 2, 4), the fixed and
-generic z transforms (nz = 1, 2, 4, 8 and 3), axes of one cell, several
-regions with empty cells, and the two-sublattice magnetoelastic path."""
+3*2^k up to the largest supported (4096 along x and along y), the pass-B
+cluster split of large ky planes (R = 2, 4), the fixed and generic z
+transforms (nz = 1, 2, 4, 8, and 3 and 16), axes of one cell, several regions
+with empty cells, and the two-sublattice magnetoelastic path."""
 import numpy as np
 import pytest
 
@@ -30,6 +31,9 @@ CASES = [
     ((1, 7, 1), (2e-9, 2e-9, 2e-9), 11, FM, 1, 0.0),
     ((9, 1, 2), (2e-9, 2e-9, 2e-9), 12, FM, 1, 0.0),
     ((40, 12, 1), (2e-9, 2e-9, 2e-9), 13, ("EXCH", "DMI", "ANIS"), 4, 0.15),   # no demag
+    ((2048, 3, 2), (2e-9, 2e-9, 1e-9), 14, FM, 1, 0.0),     # largest padded x length, 4096
+    ((3, 2048, 2), (2e-9, 2e-9, 1e-9), 15, FM, 1, 0.0),     # largest padded y length, 4096
+    ((6, 5, 16), (2e-9, 2e-9, 1e-9), 16, FM, 2, 0.05),      # largest nz with demag (generic z DFT, Pz = 32)
 ]
 
 
