@@ -150,11 +150,8 @@ inline void launch_threads(const Grid& g, int R, int* thrA, int* thrB, int* thrC
   const int Ly = g.Py / R;
   const long long elB = (long long)3 * g.nz * Ly;
   *thrB = std::min(512, std::max(64, r32(std::max(need(elB, fft_cap(Ly)), (long long)Ly))));
-  // pass C: at least 16 cells a thread in the field loop, so that a 4-row
-  // tile of a 1024-cell row runs 256 threads and two such blocks (128
-  // registers each) share an SM
   const long long fc = need((long long)g.xbc * (g.tyc >> 1) * g.Px, fft_cap(g.Px));
-  *thrC = std::min(512, std::max(std::max(128, r32(fc)), r32((long long)g.tyc * g.nx / 16)));
+  *thrC = std::min(512, std::max(std::max(128, r32(fc)), r32((long long)g.tyc * g.nx / 8)));
 }
 
 }  // namespace mmp
