@@ -212,3 +212,43 @@ def test_open_boundary_parity():
     Bn, _ = gpu_eval(mag, p)
     assert np.abs(Bn[0] - Bg[0]).max() > 100 * tolB.max()
     mag.close()
+
+
+def test_all_cells_empty():
+    """Degenerate magnet with no magnetic cell: zero field and torque, and
+    fixed steps leave the state unchanged (to FP32 renormalisation)."""
+    import torch
+    w = config_small((12, 9, 2), (2e-9, 2e-9, 1e-9), 61, terms=FM, empty_fraction=1.0)
+    p = w.problem
+    assert np.all(p.scal["MS"][0][p.regions] == 0)
+    mag = make_magnet(p, w.m0)
+    Bg, Tg = gpu_eval(mag, p)
+    assert np.all(Bg[0] == 0) and np.all(Tg[0] == 0)
+    mag.set_solver(adaptive=False, dt=1e-13)
+    mag.step(3)
+    out = torch.empty((3,) + p.shape[::-1], dtype=torch.float32, device="cuda")
+    mag.get_m(0, out)
+    m = out.cpu().numpy()
+    assert np.all(np.isfinite(m)) and np.allclose(m, w.m0[0], rtol=0, atol=1e-6)
+    mag.close()
+
+
+@pytest.mark.parametrize("open_bc", [False, True])
+def test_single_magnetic_cell(open_bc):
+    """One magnetic cell inside an empty grid: all six neighbours missing,
+    so exchange and DMI see only the boundary condition and the demag field
+    is the cell's self term."""
+    w = config_small((9, 7, 3), (2e-9, 3e-9, 1e-9), 62, terms=FM)
+    p = w.problem
+    p.regions[...] = 255
+    p.regions[1, 3, 4] = 0
+    p.set("MS", 0.0, None, 255)
+    p.open_bc = open_bc
+    mag = make_magnet(p, w.m0)
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0)
+    tolB = field_tolerance(p, Bo[0])
+    assert np.all(np.abs(Bg[0] - Bo[0]) <= tolB), np.abs(Bg[0] - Bo[0]).max()
+    assert np.all(np.abs(Tg[0] - To[0]) <= torque_tolerance(p, Bo[0], tolB))
+    assert np.count_nonzero(np.abs(Bo[0]).sum(axis=0)) == 1
+    mag.close()
