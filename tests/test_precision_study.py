@@ -182,13 +182,16 @@ def test_four_step_transform_is_the_dft(mode):
     assert np.abs(back - x).max() < 10 * bound * np.abs(x).max()
 
 
-def test_tensor_core_dft_stages_against_the_field_bar():
-    """Random state (the hardest spectrum) on 128 x 128 x 8 cells of the large
-    ferromagnet workload's cell and Ms: the FP32 FFT and split TF32 stay far
-    within 1e-5 mu0 Ms of the FP64 oracle (about 2 % and 3 % of it), split
-    BF16 and single TF32 do not (split BF16 is at 0.93 of the bar on 64^2 x 8
-    cells and above it from 128^2 x 8 on, growing with the grid)."""
-    shape, cell, Ms = (128, 128, 8), (2e-9, 2e-9, 1e-9), 1.1e6
+@pytest.mark.parametrize("shape,cell,Ms", [
+    ((128, 128, 8), (2e-9, 2e-9, 1e-9), 1.1e6),   # the large ferromagnet's cell and Ms
+    ((512, 512, 1), (2e-9, 2e-9, 2e-9), 1.4e6),   # the largest batched instance, the top of its Ms range
+], ids=["ferromagnet-128x128x8", "instance-512x512x1"])
+def test_tensor_core_dft_stages_against_the_field_bar(shape, cell, Ms):
+    """Random state (the hardest spectrum): the FP32 FFT and split TF32 stay
+    far within 1e-5 mu0 Ms of the FP64 oracle (about 2 % and 3 % of it),
+    split BF16 and single TF32 do not (split BF16 is at 0.91-0.93 of the bar
+    on 64^2 x 8 and 256 x 128 x 4 cells and above it from 128^2 x 8 on,
+    growing with the grid)."""
     m = random_unit_vectors(20241131, shape).astype(np.float64)
     M = Ms * m
     ref = demag.demag_fft(shape, cell, M)
