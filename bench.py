@@ -590,7 +590,7 @@ def run_gpu(args):
     # batch, whose lock steps replay from a CUDA graph (launch-bound grids)
     graph_path = None
     if args.workload == "c1":
-        mag.set_shape(R=1, stage_kernel=0)
+        mag.set_shape(R=1, stage_kernel=0, engine=0)
         bt = pkg.Batch(stream)
         bt.add(mag, "steps", args.warmup + args.steps)
         bt.advance(args.warmup)
@@ -657,9 +657,9 @@ def run_gpu(args):
 
 
 def parse_shape(text):
-    """--shape ty,radix_x,radix_y,R,stage_kernel[,tyc]"""
+    """--shape ty,radix_x,radix_y,R,stage_kernel[,tyc[,engine]]"""
     v = [int(x) for x in text.split(",")]
-    return dict(zip(("ty", "radix_x", "radix_y", "R", "stage_kernel", "tyc"), v))
+    return dict(zip(("ty", "radix_x", "radix_y", "R", "stage_kernel", "tyc", "engine"), v))
 
 
 def run_profile_evals(args):

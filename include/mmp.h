@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define MMP_VERSION 1
+#define MMP_VERSION 2
 
 typedef struct mmp_ctx mmp_ctx;
 
@@ -287,10 +287,19 @@ typedef struct mmp_shape {
     int stage_kernel;  /* 1: pass B stages its slice of the kernel octant in shared memory */
     int tyc;           /* rows per tile of pass C (inverse x FFT + field): 2, 4, 8, or 0 = the
                           default (ty, fewer when a block cannot hold its row pairs) */
+    int engine;        /* FFT engine, bit mask: MMP_ENGINE_WARP_B = pass B on warp-level
+                          transforms (one warp per column, in-register DFTs and one
+                          shared-memory transpose; folded y length Py/R of 256, 512 or
+                          1024, ny <= Py/R, R of 1 or 2, nz of 1, 2, 4 or 8); 0 = the
+                          block-wide Stockham passes (any supported grid).  radix_y and
+                          stage_kernel do not apply to the warp pass B. */
 } mmp_shape;
+#define MMP_ENGINE_WARP_B 1
 
 /* Current shape of the context (chosen at creation: ty from the grid, the
- * radix-16 plans, the smallest R that fits, stage_kernel = 1). */
+ * radix-16 plans; the warp pass B where it applies, with R = 2 when
+ * Py = 2048 and R = 1 below, else the smallest R that fits the block pass
+ * B with stage_kernel = 1). */
 int mmp_get_shape(mmp_ctx* ctx, mmp_shape* out);
 
 /* Set a shape.  MMP_E_INVAL (context unchanged) if it does not fit the grid
@@ -299,12 +308,12 @@ int mmp_get_shape(mmp_ctx* ctx, mmp_shape* out);
  * Runge-Kutta stage is dropped; results agree to FP32 rounding. */
 int mmp_set_shape(mmp_ctx* ctx, const mmp_shape* shape);
 
-#define MMP_TUNE_BATCH 1   /* only shapes a batch runs (R = 1, stage_kernel = 0), 8-row tiles */
+#define MMP_TUNE_BATCH 1   /* only shapes a batch runs (R = 1, stage_kernel = 0, engine = 0), 8-row tiles */
 #define MMP_TUNE_FORCE 2   /* time again even if this geometry was tuned before */
 /* Time the valid shapes on the context's current state and keep the
  * fastest: after a warm-up of ~100 ms of evaluations (loaded clocks), the
  * candidates of passes A+C (tile rows, x plan) and of pass B (R, staging,
- * y plan) are timed separately in two interleaved rounds (CUDA events per
+ * y plan, block or warp engine) are timed separately in two interleaved rounds (CUDA events per
  * pass on the context's stream, the better round counts); the combination
  * replaces the starting shape only if a longer interleaved measurement
  * finds it > 2 % faster per evaluation.  Returns the shape (chosen, may be
@@ -316,16 +325,20 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms);
 
 /* ---------------------------------------------------------------------
  * Batches: independent contexts advanced together (no counterpart in the
- * paper, which runs one simulation at a time).  Every Dormand-Prince stage
- * of all active members is one persistent kernel launch over a work list of
- * (member, tile) items; lock steps of fixed-step members are replayed from
- * a CUDA graph.  A member runs exactly the arithmetic of its own context
+ * paper, which runs one simulation at a time).  In every Dormand-Prince
+ * stage each of the three demag passes of all active members is launched
+ * once per (z group, block-size class) over a work list of (member, tile)
+ * items, one block per item, longest first; the launches of a pass run
+ * concurrently on side streams and stream order carries the dependencies
+ * between passes (there is no device-side wait).  Lock steps of
+ * fixed-step members are replayed from a CUDA graph.  A member runs
+ * exactly the arithmetic of its own context
  * (same plans and coefficients), so its results are bitwise those of
  * mmp_step / mmp_run / mmp_relax on the same context with the same shape.
  *
  * Members: one sublattice, one region (no region map), the demag term on,
- * no AFM / magnetoelastic / elastic terms, shape R = 1 and stage_kernel = 0
- * (mmp_set_shape or mmp_autotune with MMP_TUNE_BATCH first); otherwise
+ * no AFM / magnetoelastic / elastic terms, shape R = 1, stage_kernel = 0 and
+ * engine = 0 (mmp_set_shape or mmp_autotune with MMP_TUNE_BATCH first); otherwise
  * MMP_E_INVAL.  The batch borrows its members: while a context is a member
  * it must not be used elsewhere, and it must be removed before it is
  * destroyed.  Between mmp_batch_advance calls every member's state sits in
@@ -353,9 +366,7 @@ int mmp_batch_size(mmp_batch* b, int* n);
 /* Run up to max_attempts lock-step attempts; a member stops taking part
  * once its goal is reached.  Adaptive or relaxing members read their
  * error estimates back once per lock step (one synchronisation for the
- * whole batch).  n_active (may be NULL) receives the members not done.
- * MMP_E_TIMEOUT if a dependency wait inside the stage kernel ran past its
- * limit (the step is then invalid and should be discarded). */
+ * whole batch).  n_active (may be NULL) receives the members not done. */
 int mmp_batch_advance(mmp_batch* b, int max_attempts, int* n_active);
 /* done: goal reached (or failed); status: MMP_OK or the member's error
  * (MMP_E_NONFINITE: its state is the last accepted one). */

@@ -32,7 +32,8 @@ BOUNDARIES = {"neumann": 0, "open": 1}
 class Shape(ctypes.Structure):
     """mmp_shape: launch shape of the demag passes."""
     _fields_ = [("ty", ctypes.c_int), ("radix_x", ctypes.c_int), ("radix_y", ctypes.c_int),
-                ("R", ctypes.c_int), ("stage_kernel", ctypes.c_int), ("tyc", ctypes.c_int)]
+                ("R", ctypes.c_int), ("stage_kernel", ctypes.c_int), ("tyc", ctypes.c_int),
+                ("engine", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

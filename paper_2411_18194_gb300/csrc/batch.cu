@@ -170,7 +170,10 @@ bool eligible(const mmp_ctx* c, const char** why) {
     *why = "batch members have no AFM, magnetoelastic or elastic term";
     return false;
   }
-  if (c->R != 1 || c->ks != 0) { *why = "batch members use the shape R = 1, stage_kernel = 0"; return false; }
+  if (c->R != 1 || c->ks != 0 || c->engine != 0) {
+    *why = "batch members use the shape R = 1, stage_kernel = 0, engine = 0";
+    return false;
+  }
   if (c->method != MMP_DP45) { *why = "batch members use the Dormand-Prince solver"; return false; }
   const Grid& g = c->g;
   if ((long long)g.xb * (g.ty / 2) * g.Px > (long long)fft_cap_a(c->plan_x) * kBatchThreads ||

@@ -1,6 +1,7 @@
 // batch.h -- device side of the batched driver (batch.cu): the per-member
-// descriptor, work items, and the persistent pass kernels over a work
-// list (batch_a.cu, batch_b.cu, batch_c.cu).
+// descriptor, work items, and the pass kernels over a work list, one block
+// per (member, tile) item, launched once per pass, z group and block-size
+// class (batch_a.cu, batch_b.cu, batch_c.cu).
 #pragma once
 #include "kernels.h"
 

@@ -45,6 +45,7 @@ struct mmp_ctx {
   float* d_khat = nullptr;     // shared spectrum (build_khat), not owned
   std::tuple<int, int, int, int, double, double, double> khat_key;
   float2 *d_tw_x = nullptr, *d_tw_y = nullptr, *d_tw_ly = nullptr, *d_tw_z = nullptr;
+  float2* d_tw_wy = nullptr;   // warp pass B twiddles (engine & MMP_ENGINE_WARP_B)
   unsigned* d_red = nullptr;   // [0] error bits, [1] torque bits
   double* d_energy = nullptr;  // [MMP_NTERMS] (mmp_energy)
   unsigned* h_red = nullptr;   // pinned
@@ -54,6 +55,7 @@ struct mmp_ctx {
   int R = 1, thrA = 256, thrB = 256, thrC = 256;
   int ks = 1;                  // pass B stages the kernel slice in shared memory
   int radix_x = 0, radix_y = 0;   // FFT plan variants (make_plan)
+  int engine = 0;              // mmp_shape.engine
   // solver
   int method = 0;              // MMP_DP45, ... (dp45.h tableau)
   int adaptive = 0;

@@ -60,6 +60,10 @@ struct DemagArgs {
   FftPlan plan_x, plan_ly;
   int R;                     // residue classes of ky per cluster
   int ks;                    // pass B stages the kernel slice in shared memory
+  // warp engine (wfft.cuh): twiddle tables w_N^(l k1) at [k1 * 32 + l]
+  const float2* tw_wy;       // N = Ly (pass B)
+  const float2* tw_wx;       // N = nx (passes A and C)
+  int engine;                // 0: block Stockham passes, 1: warp passes
 };
 
 struct Coefs {
@@ -118,6 +122,21 @@ cudaError_t launch_assemble(const Grid& g, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_passA(const Grid& g, const StageArgs& a, const DemagArgs& d, const Coefs& c,
                          int threads, cudaStream_t s);
 cudaError_t launch_passB(const Grid& g, const DemagArgs& d, int threads, cudaStream_t s);
+// warp pass B (passb_w.cuh) for Ly = Py / R = 32 M, M in {8, 16, 32}
+template <int M>
+cudaError_t launch_passB_w_len(const Grid& g, const DemagArgs& d, cudaStream_t s);
+template <> cudaError_t launch_passB_w_len<8>(const Grid& g, const DemagArgs& d, cudaStream_t s);
+template <> cudaError_t launch_passB_w_len<16>(const Grid& g, const DemagArgs& d, cudaStream_t s);
+template <> cudaError_t launch_passB_w_len<32>(const Grid& g, const DemagArgs& d, cudaStream_t s);
+// whether the warp pass B handles this grid at residue count R
+inline bool passb_w_supported(const Grid& g, int R) {
+  if (R != 1 && R != 2) return false;
+  if (g.Py % R != 0) return false;
+  const int Ly = g.Py / R;
+  if (Ly != 256 && Ly != 512 && Ly != 1024) return false;
+  if (g.ny > Ly) return false;
+  return g.nz == 1 || g.nz == 2 || g.nz == 4 || g.nz == 8;
+}
 cudaError_t launch_field(const Grid& g, const DemagArgs& d, const Coefs& c, const FieldArgs& f,
                          int nsub, bool demag, int threads, cudaStream_t s);
 cudaError_t launch_strain(const Grid& g, const ElasticArgs& e, int nsub, cudaStream_t s);

@@ -395,6 +395,14 @@ bool shape_ok(const mmp_ctx* ctx, const mmp_shape& s, const char** why) {
     *why = "pass A or C shared memory above 227 KB";
     return false;
   }
+  if (s.engine & ~MMP_ENGINE_WARP_B) { *why = "unknown engine bits"; return false; }
+  if (s.engine & MMP_ENGINE_WARP_B) {
+    if (!passb_w_supported(g, s.R)) {
+      *why = "the warp pass B needs Py/R of 256, 512 or 1024, ny <= Py/R, R of 1 or 2 and nz of 1, 2, 4 or 8";
+      return false;
+    }
+    return true;
+  }
   if (passb_smem(g.ny, g.nz, g.Py, g.kzn, s.R, s.stage_kernel != 0).total > 227 * 1024) {
     *why = "pass B shared memory above 227 KB";
     return false;
@@ -417,6 +425,7 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
   make_plan(g.Py / s.R, ctx->plan_ly, s.radix_y);
   TRY(upload_table(ctx, ctx->d_tw_x, pass_twiddles(ctx->plan_x)));
   TRY(upload_table(ctx, ctx->d_tw_ly, pass_twiddles(ctx->plan_ly)));
+  if (s.engine & MMP_ENGINE_WARP_B) TRY(upload_table(ctx, ctx->d_tw_wy, warp_twiddles(g.Py / s.R)));
   g.ty = s.ty;
   g.tyc = s.tyc ? s.tyc : pick_tile_rows_c(s.ty, g.Px);
   // all three components in one x-FFT call when a 512-thread block holds
@@ -432,6 +441,7 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
   ctx->ks = s.stage_kernel != 0;
   ctx->radix_x = s.radix_x;
   ctx->radix_y = s.radix_y;
+  ctx->engine = s.engine;
   launch_threads(g, ctx->R, &ctx->thrA, &ctx->thrB, &ctx->thrC);
   ctx->k1_valid = false;
   ctx->config_gen++;
@@ -446,6 +456,7 @@ mmp_shape current_shape(const mmp_ctx* ctx) {
   s.radix_y = ctx->radix_y;
   s.R = ctx->R;
   s.stage_kernel = ctx->ks;
+  s.engine = ctx->engine;
   return s;
 }
 
@@ -461,6 +472,9 @@ DemagArgs demag_args(mmp_ctx* ctx) {
   d.plan_ly = ctx->plan_ly;
   d.R = ctx->R;
   d.ks = ctx->ks;
+  d.tw_wy = ctx->d_tw_wy;
+  d.tw_wx = nullptr;
+  d.engine = (ctx->engine & MMP_ENGINE_WARP_B) ? 1 : 0;
   return d;
 }
 
@@ -837,6 +851,15 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
     sh.radix_y = 0;
     sh.R = pick_residues(g);
     sh.stage_kernel = 1;
+    sh.engine = 0;
+    // the warp pass B where it applies: one CTA per plane up to Py = 1024,
+    // a two-CTA cluster at Py = 2048
+    const int Rw = g.Py > 1024 ? 2 : 1;
+    if (passb_w_supported(g, Rw)) {
+      sh.R = Rw;
+      sh.stage_kernel = 0;
+      sh.engine = MMP_ENGINE_WARP_B;
+    }
     if (sh.R == 0) rc = fail(MMP_E_INVAL, "y-z plane of %d x %d too large for pass B", ny, nz);
     else rc = apply_shape(ctx, sh);
   }
@@ -862,7 +885,7 @@ int mmp_destroy(mmp_ctx* ctx) {
     if (ev) cudaEventDestroy(ev);
   void* bufs[] = {ctx->d_regions, ctx->d_coef, ctx->d_hA, ctx->d_y, ctx->d_stage, ctx->d_B, ctx->d_eps,
                   ctx->d_sig, ctx->d_T, ctx->d_tw_x, ctx->d_tw_y, ctx->d_tw_ly, ctx->d_tw_z, ctx->d_red,
-                  ctx->d_energy};
+                  ctx->d_energy, ctx->d_tw_wy};
   for (void* p : bufs) dfree(ctx, p);
   for (int i = 0; i < 7; ++i) dfree(ctx, ctx->d_k[i]);
   if (ctx->h_red) cudaFreeHost(ctx->h_red);
@@ -1254,6 +1277,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
   if (batch) {
     start.R = 1;
     start.stage_kernel = 0;
+    start.engine = 0;
     start.ty = 8;   // the largest tiles that fit
     while (start.ty > 2 && !shape_ok(ctx, start, &why)) start.ty >>= 1;
     if (!shape_ok(ctx, start, &why)) return fail(MMP_E_INVAL, "no batch shape fits this grid: %s", why);
@@ -1286,8 +1310,18 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
         s.R = R;
         s.stage_kernel = st;
         s.radix_y = ry;
+        s.engine = 0;
         if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
       }
+  for (int R : {1, 2}) {
+    if (batch) break;
+    mmp_shape s = start;
+    s.R = R;
+    s.stage_kernel = 0;
+    s.radix_y = 0;
+    s.engine = MMP_ENGINE_WARP_B;
+    if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
+  }
   // two interleaved rounds; a candidate's time is its better round
   std::vector<double> t_ac(cand_ac.size(), 1e300), t_b(cand_b.size(), 1e300);
   for (int round = 0; round < 2; ++round) {
@@ -1317,6 +1351,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
       best.R = cand_b[i].R;
       best.stage_kernel = cand_b[i].stage_kernel;
       best.radix_y = cand_b[i].radix_y;
+      best.engine = cand_b[i].engine;
     }
   // keep the starting shape unless the combination measures faster by > 2 %
   // (longer, interleaved measurement of both)

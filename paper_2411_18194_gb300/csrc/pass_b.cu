@@ -46,6 +46,14 @@ static cudaError_t launch_passB_t(const Grid& g, const DemagArgs& d, int threads
 }
 
 cudaError_t launch_passB(const Grid& g, const DemagArgs& d, int threads, cudaStream_t s) {
+  if (d.engine == 1) {
+    switch (g.Py / d.R) {
+      case 256: return launch_passB_w_len<8>(g, d, s);
+      case 512: return launch_passB_w_len<16>(g, d, s);
+      case 1024: return launch_passB_w_len<32>(g, d, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (g.nz) {
     case 1: return launch_passB_t<1>(g, d, threads, s);
     case 2: return launch_passB_t<2>(g, d, threads, s);

@@ -14,24 +14,11 @@
 #pragma once
 #include <cooperative_groups.h>
 #include "kernels.h"
+#include "copy.cuh"
 
 namespace mmp {
 
 namespace cg = cooperative_groups;
-
-// ------------------------------------------------------------- helpers ----
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-// wait until at most one (the most recent) group is still in flight
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
-  unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
 
 // 3x3 symmetric kernel times a complex 3-vector.  K points at the six
 // components (xx, yy, zz, xy, xz, yz) of octant entry (|ky|, |kz|); sy, sz

@@ -98,6 +98,19 @@ inline int fft_cap(int L) {
 inline int fft_cap_a(const FftPlan& p) { return fft_cap(p) / 2; }
 inline int fft_cap_a(int L) { return fft_cap(L) / 2; }
 
+// Twiddle table of the warp FFT of length N = 32 M (wfft.cuh):
+// entry k1 * 32 + l = w_N^(l k1), k1 < M.  Built in FP64, rounded once.
+inline std::vector<float2> warp_twiddles(int N) {
+  const int M = N / 32;
+  std::vector<float2> w((size_t)32 * M);
+  for (int k1 = 0; k1 < M; ++k1)
+    for (int l = 0; l < 32; ++l) {
+      double a = 2.0 * 3.14159265358979323846 * (double)(l * k1) / (double)N;
+      w[k1 * 32 + l] = make_float2((float)cos(a), (float)(-sin(a)));
+    }
+  return w;
+}
+
 inline std::vector<float2> roots(int P) {
   std::vector<float2> w(P);
   for (int t = 0; t < P; ++t) {

@@ -28,7 +28,7 @@ def _magnet(i, shape, terms=("DEMAG", "EXCH")):
     p = _problem(i, shape, terms)
     m0 = random_unit_vectors(9000 + i, shape)
     mag = make_magnet(p, [m0])
-    mag.set_shape(R=1, stage_kernel=0)
+    mag.set_shape(R=1, stage_kernel=0, engine=0)
     return p, m0, mag
 
 
@@ -150,10 +150,10 @@ def test_batch_rejects_ineligible_members():
     p = _problem(0, (16, 16, 1))
     mag = make_magnet(p, [random_unit_vectors(1, (16, 16, 1))])
     with pkg.Batch() as b:
-        mag.set_shape(R=1, stage_kernel=1)
+        mag.set_shape(R=1, stage_kernel=1, engine=0)
         with pytest.raises(pkg.MmpError):
             b.add(mag, "steps", 1)
-        mag.set_shape(R=1, stage_kernel=0)
+        mag.set_shape(R=1, stage_kernel=0, engine=0)
         b.add(mag, "steps", 1)
         with pytest.raises(pkg.MmpError):
             b.add(mag, "steps", 1)      # already a member

@@ -52,6 +52,38 @@ def test_field_and_torque_parity(shape, cell, seed, terms, nreg, empty):
     mag.close()
 
 
+# Grids whose pass B runs on the warp-level transforms (folded y length
+# Py / R of 256, 512 or 1024, nz of 1, 2, 4 or 8): shape, cell, seed, terms,
+# regions, empty fraction, expected R of the default shape.
+WARP_CASES = [
+    ((5, 120, 2), (2e-9, 2e-9, 1e-9), 51, FM, 1, 0.0, 1),      # Py = 256, one CTA per plane
+    ((6, 200, 1), (2e-9, 2e-9, 2e-9), 52, FM, 2, 0.05, 1),     # Py = 512, nz = 1, regions and empty cells
+    ((4, 400, 4), (2e-9, 2e-9, 1e-9), 53, FM, 1, 0.0, 1),      # Py = 1024, nz = 4
+    ((3, 1000, 8), (2e-9, 2e-9, 1e-9), 54, FM, 1, 0.0, 2),     # Py = 2048: a two-CTA cluster per plane, ragged ny
+    ((2, 777, 2), (2e-9, 2e-9, 1e-9), 55, FM, 3, 0.1, 2),      # odd ny (8-byte copies), three regions
+]
+
+
+@pytest.mark.parametrize("shape,cell,seed,terms,nreg,empty,R", WARP_CASES,
+                         ids=["x".join(map(str, c[0])) + "-%d" % c[2] for c in WARP_CASES])
+def test_warp_pass_b_parity(shape, cell, seed, terms, nreg, empty, R):
+    """The warp-level pass B (one warp per y column, in-register DFTs, one
+    shared-memory transpose; z transform + kernel multiply per ky in
+    registers) is the default where it applies; field and torque against
+    the oracle, element by element."""
+    w = config_small(shape, cell, seed, terms=terms, n_regions=nreg, empty_fraction=empty)
+    p = w.problem
+    mag = make_magnet(p, w.m0)
+    sh = mag.get_shape()
+    assert sh["engine"] == 1 and sh["R"] == R, sh
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0)
+    tolB = field_tolerance(p, Bo[0])
+    assert np.all(np.abs(Bg[0] - Bo[0]) <= tolB), np.abs(Bg[0] - Bo[0]).max()
+    assert np.all(np.abs(Tg[0] - To[0]) <= torque_tolerance(p, Bo[0], tolB)), np.abs(Tg[0] - To[0]).max()
+    mag.close()
+
+
 def test_two_sublattice_magnetoelastic_parity():
     w = config_small((23, 18, 1), (2e-9, 2e-9, 2e-9), 31, n_sub=2,
                      terms=("DEMAG", "EXCH", "ANIS", "AFM", "MEL", "ELASTIC", "ZEEMAN"))
@@ -169,9 +201,9 @@ def test_cubic_anisotropy_parity():
 
 
 def test_every_launch_shape_matches_oracle():
-    """Every valid launch shape (pass-B residue classes R, kernel staging, y
-    plan; pass A/C tile rows) gives the same field within the bar: the shape
-    changes only the FP32 rounding order."""
+    """Every valid launch shape (pass-B engine, residue classes R, kernel
+    staging, y plan; pass A/C tile rows) gives the same field within the
+    bar: the shape changes only the FP32 rounding order."""
     import itertools
     from paper_2411_18194_gb300 import MmpError
     w = config_small((24, 256, 8), (2e-9, 2e-9, 1e-9), 21, terms=FM)
@@ -181,16 +213,17 @@ def test_every_launch_shape_matches_oracle():
     tolB = field_tolerance(p, Bo[0])
     tolT = torque_tolerance(p, Bo[0], tolB)
     seen = []
-    for R, st, ry, (ty, tyc) in itertools.product((1, 2, 4, 8), (0, 1), (0, 1), ((8, 0), (2, 4), (4, 8))):
+    for eng, R, st, ry, (ty, tyc) in itertools.product((0, 1), (1, 2, 4, 8), (0, 1), (0, 1),
+                                                       ((8, 0), (2, 4), (4, 8))):
         try:
-            mag.set_shape(R=R, stage_kernel=st, radix_y=ry, ty=ty, tyc=tyc)
+            mag.set_shape(engine=eng, R=R, stage_kernel=st, radix_y=ry, ty=ty, tyc=tyc)
         except MmpError:
             continue
-        seen.append(R)
+        seen.append((eng, R))
         Bg, Tg = gpu_eval(mag, p)
-        assert np.all(np.abs(Bg[0] - Bo[0]) <= tolB), (R, st, ry, ty, tyc, np.abs(Bg[0] - Bo[0]).max())
-        assert np.all(np.abs(Tg[0] - To[0]) <= tolT), (R, st, ry, ty, tyc)
-    assert set(seen) == {1, 2, 4, 8}
+        assert np.all(np.abs(Bg[0] - Bo[0]) <= tolB), (eng, R, st, ry, ty, tyc, np.abs(Bg[0] - Bo[0]).max())
+        assert np.all(np.abs(Tg[0] - To[0]) <= tolT), (eng, R, st, ry, ty, tyc)
+    assert set(seen) == {(0, 1), (0, 2), (0, 4), (0, 8), (1, 1), (1, 2)}
     mag.close()
 
 
