@@ -287,18 +287,23 @@ typedef struct mmp_shape {
     int stage_kernel;  /* 1: pass B stages its slice of the kernel octant in shared memory */
     int tyc;           /* rows per tile of pass C (inverse x FFT + field): 2, 4, 8, or 0 = the
                           default (ty, fewer when a block cannot hold its row pairs) */
-    int engine;        /* FFT engine, bit mask: MMP_ENGINE_WARP_B = pass B on warp-level
-                          transforms (one warp per column, in-register DFTs and one
-                          shared-memory transpose; folded y length Py/R of 256, 512 or
-                          1024, ny <= Py/R, R of 1 or 2, nz of 1, 2, 4 or 8); 0 = the
-                          block-wide Stockham passes (any supported grid).  radix_y and
-                          stage_kernel do not apply to the warp pass B. */
+    int engine;        /* FFT engine, bit mask (0 = the block-wide Stockham passes, any
+                          supported grid):
+                          MMP_ENGINE_WARP_B: pass B on warp-level transforms (one warp
+                          per column, in-register DFTs and one shared-memory transpose;
+                          folded y length Py/R of 256, 512 or 1024, ny <= Py/R, R of 1
+                          or 2, nz of 1, 2, 4 or 8); radix_y and stage_kernel do not
+                          apply to it;
+                          MMP_ENGINE_WARP_X: passes A and C on warp-level transforms in
+                          tiles of one row pair (Px = 2048, i.e. nx of 769 .. 1024);
+                          ty, tyc and radix_x do not apply to them. */
 } mmp_shape;
 #define MMP_ENGINE_WARP_B 1
+#define MMP_ENGINE_WARP_X 2
 
 /* Current shape of the context (chosen at creation: ty from the grid, the
- * radix-16 plans; the warp pass B where it applies, with R = 2 when
- * Py = 2048 and R = 1 below, else the smallest R that fits the block pass
+ * radix-16 plans; the warp passes where they apply (pass B with R = 2 when
+ * Py = 2048 and R = 1 below), else the smallest R that fits the block pass
  * B with stage_kernel = 1). */
 int mmp_get_shape(mmp_ctx* ctx, mmp_shape* out);
 

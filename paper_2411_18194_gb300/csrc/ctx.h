@@ -46,6 +46,7 @@ struct mmp_ctx {
   std::tuple<int, int, int, int, double, double, double> khat_key;
   float2 *d_tw_x = nullptr, *d_tw_y = nullptr, *d_tw_ly = nullptr, *d_tw_z = nullptr;
   float2* d_tw_wy = nullptr;   // warp pass B twiddles (engine & MMP_ENGINE_WARP_B)
+  float2 *d_tw_wx = nullptr, *d_tw_wx2 = nullptr;   // warp passes A and C (MMP_ENGINE_WARP_X)
   unsigned* d_red = nullptr;   // [0] error bits, [1] torque bits
   double* d_energy = nullptr;  // [MMP_NTERMS] (mmp_energy)
   unsigned* h_red = nullptr;   // pinned

@@ -245,26 +245,16 @@ __device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbu
   __syncthreads();
 }
 
-// Pass C of one tile: rows y0 .. y0 + ty - 1 of plane z.  `smem` is the
-// block's dynamic shared memory.
+// Local field, torque and the reductions of rows y0 .. y0 + nrows - 1 of
+// plane z (one tile): bd is the demag field of the tile, component c, row
+// `row`, cell x at bd[c * cstride + row * rstride + x].
 template <int NSUB, bool DEMAG, bool UNI>
-__device__ __forceinline__ void field_tile(float* smem, const Grid& g, const DemagArgs& d, const Coefs& co,
-                                           const FieldArgs& f, int z, int y0) {
-  const int nx = g.nx, ny = g.ny, Px = g.Px;
-  float* bd = smem;                                                     // [3][TY][nx]
-  float2* fbuf = reinterpret_cast<float2*>(smem + ((3 * g.tyc * nx + 3) & ~3));   // [NP][Px]
-  if (DEMAG) {
-    float2* tw = fbuf + g.xbc * (g.tyc >> 1) * fft_pitch(Px);
-    for (int i = threadIdx.x; i < Px; i += blockDim.x) tw[i] = __ldg(d.tw_x + i);
-    // straight-line calls, as in pass A; with xb = 3 the first does all three
-    const int rest = g.xbc == 3 ? 0 : 1;
-    inverse_x_components(0, g.xbc == 3 ? 3 : 1, fbuf, tw, bd, g, d, z, y0);
-    inverse_x_components(1, rest, fbuf, tw, bd, g, d, z, y0);
-    inverse_x_components(2, rest, fbuf, tw, bd, g, d, z, y0);
-  }
+__device__ __forceinline__ void field_cells(const float* bd, int cstride, int rstride, int nrows, const Grid& g,
+                                            const Coefs& co, const FieldArgs& f, int z, int y0) {
+  const int nx = g.nx, ny = g.ny;
   float emax = 0.0f, tmax = 0.0f;
   const long long n = g.n;
-  for (int e = threadIdx.x; e < g.tyc * nx; e += blockDim.x) {
+  for (int e = threadIdx.x; e < nrows * nx; e += blockDim.x) {
     int row = e / nx, x = e - row * nx, y = y0 + row;
     if (y >= ny) continue;
     long long cell = x + (long long)nx * (y + (long long)ny * z);
@@ -272,7 +262,7 @@ __device__ __forceinline__ void field_tile(float* smem, const Grid& g, const Dem
     float b3[3] = {0.0f, 0.0f, 0.0f};
     if (DEMAG) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) b3[c] = bd[(c * g.tyc + row) * nx + x];
+      for (int c = 0; c < 3; ++c) b3[c] = bd[c * cstride + row * rstride + x];
     }
 #pragma unroll
     for (int s = 0; s < NSUB; ++s) {
@@ -302,6 +292,26 @@ __device__ __forceinline__ void field_tile(float* smem, const Grid& g, const Dem
     float v = block_max(isnan(tmax) ? __int_as_float(0x7f800000) : tmax);
     if (threadIdx.x == 0) atomic_max_pos(f.torque_max, v);
   }
+}
+
+// Pass C of one tile: rows y0 .. y0 + ty - 1 of plane z.  `smem` is the
+// block's dynamic shared memory.
+template <int NSUB, bool DEMAG, bool UNI>
+__device__ __forceinline__ void field_tile(float* smem, const Grid& g, const DemagArgs& d, const Coefs& co,
+                                           const FieldArgs& f, int z, int y0) {
+  const int nx = g.nx, ny = g.ny, Px = g.Px;
+  float* bd = smem;                                                     // [3][TY][nx]
+  float2* fbuf = reinterpret_cast<float2*>(smem + ((3 * g.tyc * nx + 3) & ~3));   // [NP][Px]
+  if (DEMAG) {
+    float2* tw = fbuf + g.xbc * (g.tyc >> 1) * fft_pitch(Px);
+    for (int i = threadIdx.x; i < Px; i += blockDim.x) tw[i] = __ldg(d.tw_x + i);
+    // straight-line calls, as in pass A; with xb = 3 the first does all three
+    const int rest = g.xbc == 3 ? 0 : 1;
+    inverse_x_components(0, g.xbc == 3 ? 3 : 1, fbuf, tw, bd, g, d, z, y0);
+    inverse_x_components(1, rest, fbuf, tw, bd, g, d, z, y0);
+    inverse_x_components(2, rest, fbuf, tw, bd, g, d, z, y0);
+  }
+  field_cells<NSUB, DEMAG, UNI>(bd, g.tyc * nx, nx, g.tyc, g, co, f, z, y0);
 }
 
 }  // namespace mmp

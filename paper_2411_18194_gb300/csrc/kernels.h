@@ -62,8 +62,9 @@ struct DemagArgs {
   int ks;                    // pass B stages the kernel slice in shared memory
   // warp engine (wfft.cuh): twiddle tables w_N^(l k1) at [k1 * 32 + l]
   const float2* tw_wy;       // N = Ly (pass B)
-  const float2* tw_wx;       // N = nx (passes A and C)
-  int engine;                // 0: block Stockham passes, 1: warp passes
+  const float2* tw_wx;       // N = Px / 2 (passes A and C)
+  const float2* tw_wx2;      // w_Px^x, x < Px / 2 (natural order; passes A and C)
+  int engine;                // pass B: 0 block Stockham passes, 1 warp passes
 };
 
 struct Coefs {
@@ -128,6 +129,11 @@ cudaError_t launch_passB_w_len(const Grid& g, const DemagArgs& d, cudaStream_t s
 template <> cudaError_t launch_passB_w_len<8>(const Grid& g, const DemagArgs& d, cudaStream_t s);
 template <> cudaError_t launch_passB_w_len<16>(const Grid& g, const DemagArgs& d, cudaStream_t s);
 template <> cudaError_t launch_passB_w_len<32>(const Grid& g, const DemagArgs& d, cudaStream_t s);
+// warp passes A and C (xfft_w.cuh): tiles of one row pair, Px = 2048
+cudaError_t launch_passA_w(const Grid& g, const StageArgs& a, const DemagArgs& d, const Coefs& c, cudaStream_t s);
+cudaError_t launch_field_w(const Grid& g, const DemagArgs& d, const Coefs& c, const FieldArgs& f, int nsub,
+                           cudaStream_t s);
+inline bool xw_supported(const Grid& g) { return g.Px == 2048; }
 // whether the warp pass B handles this grid at residue count R
 inline bool passb_w_supported(const Grid& g, int R) {
   if (R != 1 && R != 2) return false;

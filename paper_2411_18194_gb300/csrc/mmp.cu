@@ -395,7 +395,11 @@ bool shape_ok(const mmp_ctx* ctx, const mmp_shape& s, const char** why) {
     *why = "pass A or C shared memory above 227 KB";
     return false;
   }
-  if (s.engine & ~MMP_ENGINE_WARP_B) { *why = "unknown engine bits"; return false; }
+  if (s.engine & ~(MMP_ENGINE_WARP_B | MMP_ENGINE_WARP_X)) { *why = "unknown engine bits"; return false; }
+  if ((s.engine & MMP_ENGINE_WARP_X) && !xw_supported(g)) {
+    *why = "the warp passes A and C need Px = 2048 (nx of 769 .. 1024)";
+    return false;
+  }
   if (s.engine & MMP_ENGINE_WARP_B) {
     if (!passb_w_supported(g, s.R)) {
       *why = "the warp pass B needs Py/R of 256, 512 or 1024, ny <= Py/R, R of 1 or 2 and nz of 1, 2, 4 or 8";
@@ -426,6 +430,12 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
   TRY(upload_table(ctx, ctx->d_tw_x, pass_twiddles(ctx->plan_x)));
   TRY(upload_table(ctx, ctx->d_tw_ly, pass_twiddles(ctx->plan_ly)));
   if (s.engine & MMP_ENGINE_WARP_B) TRY(upload_table(ctx, ctx->d_tw_wy, warp_twiddles(g.Py / s.R)));
+  if (s.engine & MMP_ENGINE_WARP_X) {
+    TRY(upload_table(ctx, ctx->d_tw_wx, warp_twiddles(g.Px / 2)));
+    std::vector<float2> w = roots(g.Px);
+    w.resize(g.Px / 2);
+    TRY(upload_table(ctx, ctx->d_tw_wx2, w));
+  }
   g.ty = s.ty;
   g.tyc = s.tyc ? s.tyc : pick_tile_rows_c(s.ty, g.Px);
   // all three components in one x-FFT call when a 512-thread block holds
@@ -473,7 +483,8 @@ DemagArgs demag_args(mmp_ctx* ctx) {
   d.R = ctx->R;
   d.ks = ctx->ks;
   d.tw_wy = ctx->d_tw_wy;
-  d.tw_wx = nullptr;
+  d.tw_wx = ctx->d_tw_wx;
+  d.tw_wx2 = ctx->d_tw_wx2;
   d.engine = (ctx->engine & MMP_ENGINE_WARP_B) ? 1 : 0;
   return d;
 }
@@ -524,8 +535,13 @@ int evaluate(mmp_ctx* ctx, StageArgs sa, const float* src, float* kout, float* B
   sa.nparts = ctx->nparts;
   sa.nsub = ctx->nsub;
   const float* stage = sa.stage;
+  const bool wx = demag && (ctx->engine & MMP_ENGINE_WARP_X);
   if (demag) {
-    { Traced t(ctx, MMP_K_PASS_A); CK(launch_passA(g, sa, d, co, ctx->thrA, ctx->stream), "pass A"); }
+    {
+      Traced t(ctx, MMP_K_PASS_A);
+      CK(wx ? launch_passA_w(g, sa, d, co, ctx->stream) : launch_passA(g, sa, d, co, ctx->thrA, ctx->stream),
+         "pass A");
+    }
     { Traced t(ctx, MMP_K_PASS_B); CK(launch_passB(g, d, ctx->thrB, ctx->stream), "pass B"); }
   } else if (sa.y) {
     Traced t(ctx, MMP_K_ASSEMBLE);
@@ -557,7 +573,12 @@ int evaluate(mmp_ctx* ctx, StageArgs sa, const float* src, float* kout, float* B
   }
   f.relax = relax;
   f.torque_max = tmax;
-  { Traced t(ctx, MMP_K_FIELD); CK(launch_field(g, d, co, f, ctx->nsub, demag, ctx->thrC, ctx->stream), "field"); }
+  {
+    Traced t(ctx, MMP_K_FIELD);
+    CK(wx ? launch_field_w(g, d, co, f, ctx->nsub, ctx->stream)
+          : launch_field(g, d, co, f, ctx->nsub, demag, ctx->thrC, ctx->stream),
+       "field");
+  }
   if (elastic) {
     Traced t(ctx, MMP_K_ELASTIC);
     CK(launch_elastic_rhs(g, ea, co, ctx->nsub, ctx->stream), "elastic");
@@ -860,6 +881,7 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
       sh.stage_kernel = 0;
       sh.engine = MMP_ENGINE_WARP_B;
     }
+    if (xw_supported(g)) sh.engine |= MMP_ENGINE_WARP_X;
     if (sh.R == 0) rc = fail(MMP_E_INVAL, "y-z plane of %d x %d too large for pass B", ny, nz);
     else rc = apply_shape(ctx, sh);
   }
@@ -885,7 +907,7 @@ int mmp_destroy(mmp_ctx* ctx) {
     if (ev) cudaEventDestroy(ev);
   void* bufs[] = {ctx->d_regions, ctx->d_coef, ctx->d_hA, ctx->d_y, ctx->d_stage, ctx->d_B, ctx->d_eps,
                   ctx->d_sig, ctx->d_T, ctx->d_tw_x, ctx->d_tw_y, ctx->d_tw_ly, ctx->d_tw_z, ctx->d_red,
-                  ctx->d_energy, ctx->d_tw_wy};
+                  ctx->d_energy, ctx->d_tw_wy, ctx->d_tw_wx, ctx->d_tw_wx2};
   for (void* p : bufs) dfree(ctx, p);
   for (int i = 0; i < 7; ++i) dfree(ctx, ctx->d_k[i]);
   if (ctx->h_red) cudaFreeHost(ctx->h_red);
@@ -1300,8 +1322,14 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
         s.ty = ty;
         s.tyc = tyc;
         s.radix_x = rx;
+        s.engine &= ~MMP_ENGINE_WARP_X;
         if (shape_ok(ctx, s, &why)) cand_ac.push_back(s);
       }
+  if (!batch) {
+    mmp_shape s = start;
+    s.engine |= MMP_ENGINE_WARP_X;
+    if (shape_ok(ctx, s, &why)) cand_ac.push_back(s);
+  }
   for (int R : {1, 2, 4, 8})
     for (int st = 0; st < 2; ++st)
       for (int ry = 0; ry < 2; ++ry) {
@@ -1310,7 +1338,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
         s.R = R;
         s.stage_kernel = st;
         s.radix_y = ry;
-        s.engine = 0;
+        s.engine &= ~MMP_ENGINE_WARP_B;
         if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
       }
   for (int R : {1, 2}) {
@@ -1319,7 +1347,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
     s.R = R;
     s.stage_kernel = 0;
     s.radix_y = 0;
-    s.engine = MMP_ENGINE_WARP_B;
+    s.engine |= MMP_ENGINE_WARP_B;
     if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
   }
   // two interleaved rounds; a candidate's time is its better round
@@ -1344,6 +1372,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
       best.ty = cand_ac[i].ty;
       best.tyc = cand_ac[i].tyc;
       best.radix_x = cand_ac[i].radix_x;
+      best.engine = (best.engine & ~MMP_ENGINE_WARP_X) | (cand_ac[i].engine & MMP_ENGINE_WARP_X);
     }
   for (size_t i = 0; i < cand_b.size(); ++i)
     if (t_b[i] < best_b) {
@@ -1351,7 +1380,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
       best.R = cand_b[i].R;
       best.stage_kernel = cand_b[i].stage_kernel;
       best.radix_y = cand_b[i].radix_y;
-      best.engine = cand_b[i].engine;
+      best.engine = (best.engine & ~MMP_ENGINE_WARP_B) | (cand_b[i].engine & MMP_ENGINE_WARP_B);
     }
   // keep the starting shape unless the combination measures faster by > 2 %
   // (longer, interleaved measurement of both)

@@ -84,6 +84,81 @@ def test_warp_pass_b_parity(shape, cell, seed, terms, nreg, empty, R):
     mag.close()
 
 
+# Grids whose passes A and C run on the warp-level x transforms (Px = 2048,
+# nx of 769 .. 1024): shape, cell, seed, terms, regions, empty fraction.
+WARPX_CASES = [
+    ((1000, 6, 2), (2e-9, 2e-9, 1e-9), 61, FM, 1, 0.0),      # 16-byte stage loads (nx % 4 == 0)
+    ((999, 5, 1), (2e-9, 2e-9, 2e-9), 62, FM, 2, 0.05),     # odd nx (one cell per load), odd ny (last pair of one row)
+    ((1024, 7, 3), (2e-9, 2e-9, 1e-9), 63, FM, 3, 0.1),     # nx = N exactly, generic z, regions and empty cells
+    ((800, 120, 2), (2e-9, 2e-9, 1e-9), 64, FM, 1, 0.0),    # with the warp pass B as well
+]
+
+
+@pytest.mark.parametrize("shape,cell,seed,terms,nreg,empty", WARPX_CASES,
+                         ids=["x".join(map(str, c[0])) + "-%d" % c[2] for c in WARPX_CASES])
+def test_warp_x_passes_parity(shape, cell, seed, terms, nreg, empty):
+    """Passes A and C on the warp-level x transforms (tiles of one row pair:
+    the even and odd halves of the padded transform, one warp each per
+    component) are the default for Px = 2048; field and torque against the
+    oracle, element by element."""
+    w = config_small(shape, cell, seed, terms=terms, n_regions=nreg, empty_fraction=empty)
+    p = w.problem
+    mag = make_magnet(p, w.m0)
+    assert mag.get_shape()["engine"] & 2
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0)
+    tolB = field_tolerance(p, Bo[0])
+    assert np.all(np.abs(Bg[0] - Bo[0]) <= tolB), np.abs(Bg[0] - Bo[0]).max()
+    assert np.all(np.abs(Tg[0] - To[0]) <= torque_tolerance(p, Bo[0], tolB)), np.abs(Tg[0] - To[0]).max()
+    mag.close()
+
+
+def test_warp_x_two_sublattice_magnetoelastic_parity():
+    """The two-sublattice magnetoelastic path on the warp x passes (summed M
+    in pass A, both sublattices' local fields in pass C)."""
+    w = config_small((1024, 4, 1), (2e-9, 2e-9, 2e-9), 65, n_sub=2,
+                     terms=("DEMAG", "EXCH", "ANIS", "AFM", "MEL", "ELASTIC", "ZEEMAN"))
+    p = w.problem
+    p.set("DIND", 0.0)
+    rng = np.random.default_rng(6)
+    u = (rng.normal(size=(3, 1, 4, 1024)) * 2e-12).astype(np.float32)
+    mag = make_magnet(p, w.m0, u, np.zeros_like(u))
+    assert mag.get_shape()["engine"] & 2
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0, u)
+    for s in range(2):
+        tolB = field_tolerance(p, Bo[s])
+        assert np.all(np.abs(Bg[s] - Bo[s]) <= tolB), (s, np.abs(Bg[s] - Bo[s]).max())
+        assert np.all(np.abs(Tg[s] - To[s]) <= torque_tolerance(p, Bo[s], tolB)), s
+    mag.close()
+
+
+def test_warp_x_trajectory_matches_oracle_and_block_engine():
+    """Stage assembly (including the renormalised last stage) runs in the
+    warp pass A: 20 fixed Dormand-Prince steps against the oracle, and the
+    same steps on the block engine agree to FP32 rounding."""
+    import torch
+    from oracle.dp45 import Oracle, State
+    w = config_small((1000, 6, 2), (2e-9, 2e-9, 1e-9), 66, terms=FM)
+    p = w.problem
+    dt = 2e-14
+    out = []
+    for engine in (2, 0):
+        mag = make_magnet(p, w.m0)
+        if engine != 2:
+            mag.set_shape(engine=engine)
+        assert mag.get_shape()["engine"] == engine
+        mag.set_solver(adaptive=False, dt=dt)
+        mag.step(20)
+        m = torch.empty((3,) + p.shape[::-1], dtype=torch.float32, device="cuda")
+        mag.get_m(0, m)
+        out.append(m.cpu().numpy().astype(np.float64))
+        mag.close()
+    st = Oracle(p).run_fixed(State([m.astype(np.float64) for m in w.m0]), dt, 20)
+    assert np.abs(out[0] - st.ms[0]).max() <= 1e-4
+    assert np.abs(out[0] - out[1]).max() <= 1e-5
+
+
 def test_two_sublattice_magnetoelastic_parity():
     w = config_small((23, 18, 1), (2e-9, 2e-9, 2e-9), 31, n_sub=2,
                      terms=("DEMAG", "EXCH", "ANIS", "AFM", "MEL", "ELASTIC", "ZEEMAN"))
