@@ -12,12 +12,16 @@ A member computes exactly what the same context computes alone (same shape,
 same FP32 stage coefficients, same FP64 step control), so a request's result
 is bitwise the same in the mix and served by itself.
 
-Memory accounting per request (bytes, FP32 state): the state, six stage
-vectors and the stage buffer (9 x 12 B per cell), the x-transformed spectrum
-(3 nz ny (Px/2 + 1) complex64), the coefficient table, and for a grid whose
-demag kernel spectrum is not yet resident, the spectrum (shared by requests
-of the same grid and cell size) plus its FP64 build buffers while it is
-built.
+Memory accounting (bytes, FP32 state), what stays resident:
+* per request, while it runs: the state, six stage vectors and the stage
+  buffer (9 x 12 B per cell), the x-transformed spectrum (3 nz ny (Px/2 + 1)
+  complex64) and the coefficient table;
+* per (grid, cell size), while any request of it runs: the demag kernel
+  spectrum, which the library shares between those contexts and frees with
+  the last of them.
+A request whose kernel spectrum is not resident also needs the FP64 build
+buffers during its admission (the build synchronises and frees them before
+the request joins), so they count against the budget at admission only.
 """
 import collections
 import time
@@ -40,16 +44,40 @@ def _nice(n):
     return min(p2, p3)
 
 
-def request_bytes(shape, spectrum_resident):
+def _dims(shape):
     nx, ny, nz = shape
-    n = nx * ny * nz
     Px, Py, Pz = _nice(nx), _nice(ny), _nice(nz)
-    kxn, kyn, kzn = Px // 2 + 1, Py // 2 + 1, Pz // 2 + 1
+    return nx * ny * nz, Px // 2 + 1, Py // 2 + 1, Pz // 2 + 1
+
+
+def state_bytes(shape):
+    """Resident bytes of one request while it runs (its own buffers)."""
+    nx, ny, nz = shape
+    n, kxn, _, _ = _dims(shape)
+    return 9 * 12 * n + 3 * nz * ny * kxn * 8 + 2 * 256 * 160 + 64 * 1024
+
+
+def spectrum_bytes(shape):
+    """The demag kernel spectrum of a (grid, cell size), shared by its requests."""
+    _, kxn, kyn, kzn = _dims(shape)
     krow = (6 * kzn + 3) // 4 * 4
-    b = 9 * 12 * n + 3 * nz * ny * kxn * 8 + 2 * 256 * 160 + 64 * 1024
+    return kxn * kyn * krow * 4
+
+
+def build_bytes(shape):
+    """FP64 buffers of the kernel-spectrum build (freed when the build ends)."""
+    nx, ny, nz = shape
+    n, kxn, kyn, kzn = _dims(shape)
+    ext = max(n, kxn * ny * nz, kxn * kyn * nz, kxn * kyn * kzn)
+    return 2 * 6 * 8 * ext
+
+
+def request_bytes(shape, spectrum_resident):
+    """Peak bytes a request needs at admission: its state, plus the spectrum
+    and its build buffers when the spectrum is not resident yet."""
+    b = state_bytes(shape)
     if not spectrum_resident:
-        ext = max(n, kxn * ny * nz, kxn * kyn * nz, kxn * kyn * kzn)
-        b += kxn * kyn * krow * 4 + 2 * 6 * 8 * ext
+        b += spectrum_bytes(shape) + build_bytes(shape)
     return b
 
 
@@ -93,8 +121,8 @@ class RelaxServer:
         self.queue = collections.deque()
         self.active = []
         self.finished = []
-        self.used = 0.0
-        self.spectra = collections.Counter()      # (shape, cell) -> resident users
+        self.used = 0.0                           # resident bytes: states + resident spectra
+        self.spectra = collections.Counter()      # (shape, cell) -> requests using its spectrum
         self.peak_members = 0
 
     def submit(self, req):
@@ -107,14 +135,15 @@ class RelaxServer:
     def _admit(self, now):
         while self.queue and self.queue[0].arrival <= now:
             req = self.queue[0]
-            need = request_bytes(req.workload.problem.shape, self.spectra[self._key(req)] > 0)
-            if self.active and self.used + need > self.budget:
+            key, shape = self._key(req), req.workload.problem.shape
+            new = self.spectra[key] == 0
+            if self.active and self.used + request_bytes(shape, not new) > self.budget:
                 break                                  # wait for memory (FIFO)
             self.queue.popleft()
-            req.mag = _make_magnet(req.workload, self.dt0)
-            req.bytes = need
-            self.used += need
-            self.spectra[self._key(req)] += 1
+            req.mag = _make_magnet(req.workload, self.dt0)   # builds the spectrum if new (and frees the buffers)
+            req.bytes = state_bytes(shape)
+            self.used += req.bytes + (spectrum_bytes(shape) if new else 0)
+            self.spectra[key] += 1
             self.batch.add(req.mag, "relax", req.torque_tol, req.max_time)
             req.admitted = now
             self.active.append(req)
@@ -135,7 +164,10 @@ class RelaxServer:
             req.mag.close()
             req.mag = None
             self.used -= req.bytes
-            self.spectra[self._key(req)] -= 1
+            key = self._key(req)
+            self.spectra[key] -= 1
+            if self.spectra[key] == 0:                 # the library freed the shared spectrum
+                self.used -= spectrum_bytes(req.workload.problem.shape)
             self.finished.append(req)
         self.active = keep
 

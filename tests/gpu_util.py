@@ -7,13 +7,33 @@ from inputs import GAMMA, MU0
 F32_EPS = 2.0 ** -24   # half an FP32 ulp, relative
 
 
-def field_tolerance(problem, B_ref):
-    """Per-evaluation field bar: 1e-5 mu0 Ms (the stated tolerance, read as an
-    H error of 1e-5 Ms), plus the unavoidable rounding of an FP32 output,
-    half an ulp of |B| (only matters where |B| exceeds ~1e2 T, e.g. the
-    homogeneous AFM exchange field of ~2e3 T)."""
-    ms = problem.scal["MS"].max()
-    return 1e-5 * MU0 * ms + F32_EPS * np.abs(B_ref)
+def cell_ms(problem, sub=0):
+    """Ms of sublattice `sub` at every cell, [nz][ny][nx]; a cell with Ms = 0
+    (empty) takes the largest Ms among its six neighbours (the scale of the
+    fields around it), or the largest of the problem if they are empty too."""
+    ms = problem.scal["MS"][sub][problem.regions].astype(np.float64)
+    empty = ms == 0
+    if not empty.any():
+        return ms
+    nb = np.zeros_like(ms)
+    for ax in range(3):
+        for d in (-1, 1):
+            sh = np.roll(ms, d, axis=ax)
+            idx = [slice(None)] * 3
+            idx[ax] = 0 if d == 1 else -1     # the wrapped row is not a neighbour
+            sh[tuple(idx)] = 0.0
+            nb = np.maximum(nb, sh)
+    nb = np.where(nb > 0, nb, problem.scal["MS"].max())
+    return np.where(empty, nb, ms)
+
+
+def field_tolerance(problem, B_ref, sub=0):
+    """Per-evaluation field bar, per cell: 1e-5 mu0 Ms of the cell's own
+    sublattice and region (the stated tolerance, read as an H error of
+    1e-5 Ms), plus the unavoidable rounding of an FP32 output, half an ulp
+    of |B| (only matters where |B| exceeds ~1e2 T, e.g. the homogeneous AFM
+    exchange field of ~2e3 T)."""
+    return 1e-5 * MU0 * cell_ms(problem, sub)[None] + F32_EPS * np.abs(B_ref)
 
 
 def torque_tolerance(problem, B_ref, tol_B):

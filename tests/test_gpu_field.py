@@ -127,7 +127,7 @@ def test_warp_x_two_sublattice_magnetoelastic_parity():
     Bg, Tg = gpu_eval(mag, p)
     Bo, To = oracle_eval(p, w.m0, u)
     for s in range(2):
-        tolB = field_tolerance(p, Bo[s])
+        tolB = field_tolerance(p, Bo[s], s)
         assert np.all(np.abs(Bg[s] - Bo[s]) <= tolB), (s, np.abs(Bg[s] - Bo[s]).max())
         assert np.all(np.abs(Tg[s] - To[s]) <= torque_tolerance(p, Bo[s], tolB)), s
     mag.close()
@@ -171,7 +171,7 @@ def test_two_sublattice_magnetoelastic_parity():
     Bg, Tg = gpu_eval(mag, p)
     Bo, To = oracle_eval(p, w.m0, u)
     for s in range(2):
-        tolB = field_tolerance(p, Bo[s])
+        tolB = field_tolerance(p, Bo[s], s)
         assert np.all(np.abs(Bg[s] - Bo[s]) <= tolB), (s, np.abs(Bg[s] - Bo[s]).max())
         tolT = torque_tolerance(p, Bo[s], tolB)
         assert np.all(np.abs(Tg[s] - To[s]) <= tolT), (s, np.abs(Tg[s] - To[s]).max())
@@ -246,7 +246,7 @@ def test_ferrimagnet_unequal_sublattices():
     Bg, Tg = gpu_eval(mag, p)
     Bo, To = oracle_eval(p, [m.astype(np.float64) for m in w.m0])
     for s in range(2):
-        assert np.all(np.abs(Bg[s] - Bo[s]) <= field_tolerance(p, Bo[s])), s
+        assert np.all(np.abs(Bg[s] - Bo[s]) <= field_tolerance(p, Bo[s], s)), s
     dt = 2e-15
     mag.set_solver(adaptive=False, dt=dt)
     mag.step(20)

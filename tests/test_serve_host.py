@@ -92,6 +92,32 @@ def test_fifo_admission_under_budget_and_release(server):
         assert r.admitted >= r.arrival and r.done > r.admitted and r.mag is None
 
 
+def test_spectrum_charged_per_geometry_and_build_buffers_at_admission_only(server):
+    """The shared kernel spectrum stays charged while any request of its
+    geometry runs and is released with the last one; the FP64 build buffers
+    count only against the admission of the request that builds it."""
+    shape = (128, 128, 1)
+    reqs = [server.Request(0, W(shape, need=40), 0.0, 1e-3, 1e-10),
+            server.Request(1, W(shape, need=8), 0.0, 1e-3, 1e-10)]
+    srv = server.RelaxServer(budget_bytes=1e12, attempts_per_round=4)
+    for r in reqs:
+        srv.submit(r)
+    srv._admit(0.0)
+    st, sp = server.state_bytes(shape), server.spectrum_bytes(shape)
+    assert len(srv.active) == 2
+    assert srv.used == pytest.approx(2 * st + sp)       # no build buffers after admission
+    for _ in range(3):                                  # request 1 (8 attempts) finishes first
+        srv.batch.advance(srv.attempts)
+    srv._retire(1.0)
+    assert [r.id for r in srv.active] == [0]
+    assert srv.used == pytest.approx(st + sp)           # spectrum still resident for request 0
+    for _ in range(10):
+        srv.batch.advance(srv.attempts)
+    srv._retire(2.0)
+    assert not srv.active and srv.used == pytest.approx(0.0)
+    assert server.request_bytes(shape, False) == st + sp + server.build_bytes(shape)
+
+
 def test_late_arrivals_join_while_others_run(server):
     reqs = [server.Request(0, W((64, 64, 1), need=400), 0.0, 1e-3, 1e-10),
             server.Request(1, W((64, 64, 1), need=8), 0.05, 1e-3, 1e-10)]
