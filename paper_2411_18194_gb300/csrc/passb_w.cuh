@@ -56,22 +56,36 @@ __device__ __forceinline__ void kmul3(float2 k01, float2 k23, float2 k45, float 
   c = hc;
 }
 
-// Kernel rows of one ky column from global memory (read-only path).
+// Kernel row of one ky column from global memory (read-only path), loaded
+// whole with 16-byte loads (rows are krow = 6 kzn rounded up to 4 floats,
+// 16-byte aligned) before the z transforms start.
+template <int NZ>
 struct RowsGlobal {
-  const float2* K2;   // row of (kx, |ky|): kz = 0..NZ entries of 6 floats
+  static constexpr int KQ = (6 * (NZ + 1) + 3) / 4;   // float4 per row (kzn = NZ + 1)
+  float4 q[KQ];
+  __device__ __forceinline__ explicit RowsGlobal(const float* row) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int j = 0; j < KQ; ++j) q[j] = __ldg(r4 + j);
+  }
+  __device__ __forceinline__ float at(int i) const {   // compile-time i after unrolling
+    const float4& v = q[i >> 2];
+    return (i & 3) == 0 ? v.x : (i & 3) == 1 ? v.y : (i & 3) == 2 ? v.z : v.w;
+  }
+  __device__ __forceinline__ float2 pair(int kz, int u) const { return make_float2(at(6 * kz + 2 * u), at(6 * kz + 2 * u + 1)); }
   template <int N0>
   __device__ __forceinline__ void even(float2 (&k)[N0][3]) const {
 #pragma unroll
     for (int i = 0; i < N0; ++i)
 #pragma unroll
-      for (int u = 0; u < 3; ++u) k[i][u] = __ldg(K2 + 3 * (2 * i) + u);
+      for (int u = 0; u < 3; ++u) k[i][u] = pair(2 * i, u);
   }
   template <int N1>
   __device__ __forceinline__ void odd(float2 (&k)[N1][3]) const {
 #pragma unroll
     for (int i = 0; i < N1; ++i)
 #pragma unroll
-      for (int u = 0; u < 3; ++u) k[i][u] = __ldg(K2 + 3 * (2 * i + 1) + u);
+      for (int u = 0; u < 3; ++u) k[i][u] = pair(2 * i + 1, u);
   }
 };
 // z stage of one ky column for NZ in {1, 2, 4, 8} (Pz = 2 NZ, or 1 when
@@ -258,7 +272,7 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
   for (int kp = threadIdx.x; kp < Ly; kp += NT) {
     const int ky = R * kp + r;
     const int iky = ky <= Py / 2 ? ky : Py - ky;
-    RowsGlobal rows{reinterpret_cast<const float2*>(kbase + (long long)iky * g.krow)};
+    const RowsGlobal<NZ> rows(kbase + (long long)iky * g.krow);
     zstage_w<NZ>(W, LP, kp, rows, ky <= Py / 2 ? 1.0f : -1.0f);
   }
   __syncthreads();

@@ -99,13 +99,14 @@ __device__ __forceinline__ void dft_m(float2 (&t)[M]) {
 // = w_N^(l k1), k1 < M (built on the host in FP64, rounded once).
 __host__ __device__ __forceinline__ int wfft_twiddles(int M) { return 32 * M; }
 
-// Warp FFT of B = 32 / M transforms of length N = 32 M.
+// Forward warp FFT of B = 32 / M transforms of length N = 32 M.
 // On entry lane l holds v[b M + m] = x_b[l + 32 m].
 // On exit lane j holds v[k2] = X_b[k1 + M k2] with b = j / M, k1 = j mod M.
 // `scr`: the warp's 1024 float2 of shared memory (free on entry; holds
 // nothing on exit).  `twT`: the twiddle table above (shared memory).
-template <int M, bool INV>
-__device__ __forceinline__ void wfft(float2 (&v)[32], float2* scr, const float2* twT) {
+template <int M>
+__device__ __forceinline__ void wfft_fwd(float2 (&v)[32], float2* scr, const float2* twT) {
+  constexpr bool INV = false;
   constexpr int B = 32 / M;
   const int l = lane_id();
 #pragma unroll
@@ -134,6 +135,24 @@ __device__ __forceinline__ void wfft(float2 (&v)[32], float2* scr, const float2*
   for (int c = 0; c < 32; ++c) v[c] = scr[l * 32 + (c ^ l)];
   __syncwarp();
   dft32<INV>(v);
+}
+
+// Forward (INV = false) or inverse (INV = true, exp(+2 pi i k n / N), no
+// 1/N) warp FFT, same data layout.  The inverse is the conjugate of the
+// forward transform of the conjugate, so one unrolled body serves both
+// (the negations fold into the neighbouring additions and stores); the
+// kernels are large enough for instruction fetch to matter.
+template <int M, bool INV>
+__device__ __forceinline__ void wfft(float2 (&v)[32], float2* scr, const float2* twT) {
+  if (INV) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i].y = -v[i].y;
+  }
+  wfft_fwd<M>(v, scr, twT);
+  if (INV) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i].y = -v[i].y;
+  }
 }
 
 }  // namespace mmp

@@ -171,6 +171,43 @@ def test_two_sublattice_magnetoelastic_trajectory():
     mag.close()
 
 
+def test_c3_full_size_parity_and_trajectory():
+    """The antiferromagnet + magnetoelastic + elastic workload at its own size
+    (1024x256x1, two sublattices, m = +-x with 1 degree of seeded noise, a
+    small seeded displacement u): B and tau of both sublattices element by
+    element against the oracle, then 20 fixed steps of dt = 5e-15 s with
+    max |dm| <= 1e-4 and max |du| / max |u| <= 1e-3."""
+    import torch
+    from oracle.dp45 import Oracle, State
+    w = config_c3()
+    p = w.problem
+    nx, ny, nz = p.shape
+    rng = np.random.default_rng(7)
+    u = (rng.normal(size=(3, nz, ny, nx)) * 2e-12).astype(np.float32)
+    v = np.zeros_like(u)
+    mag = make_magnet(p, w.m0, u, v)
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0, u)
+    from gpu_util import torque_tolerance
+    for s in range(2):
+        tolB = field_tolerance(p, Bo[s], s)
+        assert np.all(np.abs(Bg[s] - Bo[s]) <= tolB), (s, np.abs(Bg[s] - Bo[s]).max())
+        assert np.all(np.abs(Tg[s] - To[s]) <= torque_tolerance(p, Bo[s], tolB)), s
+    nsteps = 20
+    mag.set_solver(adaptive=False, dt=w.dt)
+    mag.step(nsteps)
+    mg = [_get_m(mag, p, s) for s in range(2)]
+    ug = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    vg = torch.empty_like(ug)
+    mag.get_elastic(ug, vg)
+    mag.close()
+    st = Oracle(p).run_fixed(State(w.m0, u, v), w.dt, nsteps)
+    for s in range(2):
+        assert np.abs(mg[s] - st.ms[s]).max() <= 1e-4, s
+    du = np.abs(ug.cpu().numpy() - st.u).max() / np.abs(st.u).max()
+    assert du <= 1e-3, du
+
+
 def test_c2_full_size_sampled_parity():
     """The large ferromagnet at full size (1024x1024x8) in the launch
     configuration the benchmark times: B_eff at sampled cells against the
