@@ -264,12 +264,20 @@ WORKLOADS = {
 
 
 def run_serve(args):
+    """C5 as its own benchmark line."""
+    line = serve_measure(args, init=True)
+    if line is not None:
+        print(json.dumps(line))
+
+
+def serve_measure(args, init):
     """C5: continuous-batching relax server against the plain path (each
-    request relaxed alone, in arrival order) on the same request stream."""
+    request relaxed alone, in arrival order) on the same request stream.
+    Returns the benchmark line on rank 0 (None elsewhere)."""
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if ws > 1:
+    if ws > 1 and init:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from inputs import serve_requests
@@ -312,29 +320,37 @@ def run_serve(args):
                        "peak_members": peak, "parallelism": "replicas",
                        "step": "one request (relax solve)"},
             "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"]},
+            "time_capped_fraction": st["time_capped_fraction"],
             "plain_path": {"solves_per_s": plain["solves_per_s"], "p50": plain["p50_s"], "p99": plain["p99_s"],
-                           "mean": plain["mean_s"], "what": "each request relaxed alone (mmp_relax) in arrival order"},
+                           "mean": plain["mean_s"], "time_capped_fraction": plain["time_capped_fraction"],
+                           "what": "each request relaxed alone (mmp_relax) in arrival order"},
             "speedup_vs_plain": (solves / span) / plain["solves_per_s"],
             "clocks": clk,
         }
-        print(json.dumps(line))
-    if ws > 1:
+    if ws > 1 and init:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 def run_batch(args):
+    """C4 as its own benchmark line."""
+    line = batch_measure(args, init=True)
+    if line is not None:
+        print(json.dumps(line))
+
+
+def batch_measure(args, init):
     """C4: the batch path against the plain one-at-a-time path on the same
-    instances (same shapes, same steps; results are bitwise equal)."""
+    instances (same shapes, same steps; results are bitwise equal).
+    Returns the benchmark line on rank 0 (None elsewhere)."""
     import numpy as np
     import torch
     ws, rank, local = dist_env()
-    if ws > 1:
+    torch.cuda.set_device(local)
+    if ws > 1 and init:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
     import paper_2411_18194_gb300 as pkg
     from inputs import batch_instances
     insts = batch_instances(args.instances)
@@ -471,10 +487,51 @@ def run_batch(args):
             "gpu_launches": launches,
             "clocks": clk,
         }
-        print(json.dumps(line))
-    if ws > 1:
+    if ws > 1 and init:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+# the batched and served halves of the metric as they ride along the default
+# line: their own workloads, compact (bounded run time)
+EXTRA_C4 = {"instances": 256, "steps": 10, "warmup": 3}
+EXTRA_C5 = {"requests": 12, "rate": 200.0, "torque_tol": 1e-4, "max_time": 1e-8, "budget_gb": 150.0,
+            "attempts": 4, "warmup": 3}
+
+
+def extras(args):
+    """Compact batched (C4) and served (C5) sub-objects of the default line."""
+    import argparse
+    a4 = argparse.Namespace(**vars(args))
+    a4.__dict__.update(EXTRA_C4)
+    l4 = batch_measure(a4, init=False)
+    a5 = argparse.Namespace(**vars(args))
+    a5.__dict__.update(EXTRA_C5)
+    l5 = serve_measure(a5, init=False)
+    if l4 is None or l5 is None:
+        return None
+    batched = {
+        "workload": WORKLOADS["c4"], "instances": l4["config"]["instances"], "steps": l4["steps"],
+        "solve": l4["solves_per_s"]["solve"],
+        "solves_per_s": l4["solves_per_s"]["batched"], "plain_solves_per_s": l4["solves_per_s"]["plain"],
+        "mcell_evals_per_s": l4["value"], "plain_mcell_evals_per_s": l4["plain_path"]["value"],
+        "speedup_vs_plain": l4["speedup_vs_plain"], "ms_per_lock_step": l4["ms_per_step"],
+        "roofline_frac": l4["roofline"]["frac"], "clocks": l4["clocks"],
+        "what": "all instances advanced together (one launch per pass per stage, lock steps from a CUDA "
+                "graph) against the same instances stepped one at a time; results bitwise equal"}
+    served = {
+        "workload": WORKLOADS["c5"], "requests": l5["config"]["requests"],
+        "torque_tol_T": l5["config"]["torque_tol_T"], "max_time_s": l5["config"]["max_time_s"],
+        "solves_per_s": l5["value"], "p50_s": l5["latency_s"]["p50"], "p99_s": l5["latency_s"]["p99"],
+        "time_capped_fraction": l5["time_capped_fraction"],
+        "plain_solves_per_s": l5["plain_path"]["solves_per_s"], "plain_p50_s": l5["plain_path"]["p50"],
+        "plain_p99_s": l5["plain_path"]["p99"], "speedup_vs_plain": l5["speedup_vs_plain"],
+        "peak_members": l5["config"]["peak_members"], "clocks": l5["clocks"],
+        "what": "continuous batching (admission by memory budget, joins between lock steps) against each "
+                "request relaxed alone in arrival order; a solve relaxes to max|m x B| <= torque tol or "
+                "the max simulated time"}
+    return {"batched": batched, "served": served}
 
 
 def run_gpu(args):
@@ -647,10 +704,28 @@ def run_gpu(args):
             "fp32_gflop_per_eval": round(eval_flops(g, p.n_sub) / 1e9, 3),
             "fp32_gflops": round(rate * eval_flops(g, p.n_sub) / 1e9, 1),
         }
+        # the ALU ceiling: measured FP32 FMA throughput (dependent-free FMA
+        # chains at full occupancy, CUDA events), with the clock seen meanwhile
+        fsamp = ClockSampler(local)
+        fsamp.start()
+        pk_gflops, pk_ms = pkg.fp32_peak(reps=200)
+        fclk = fsamp.stop()
+        line["path"]["fp32_peak_gflops"] = round(pk_gflops, 1)
+        line["path"]["fp32_frac"] = round(line["path"]["fp32_gflops"] / pk_gflops, 4)
+        line["path"]["fp32_peak_clock"] = fclk
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        line["path"]["fp32_peak_how"] = ("mmp_fp32_peak: best of 200 launches of 8 independent FMA chains per "
+                                         "thread, %d blocks x 256 threads, %.3f ms each" % (8 * nsm, pk_ms))
         if graph_path:
             line["graph_path"] = graph_path
-        print(json.dumps(line))
     mag.close()
+    del mag
+    if args.workload == "c2" and not args.no_extras:
+        ex = extras(args)
+        if rank == 0 and ex is not None:
+            line.update(ex)
+    if rank == 0:
+        print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -690,6 +765,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="c2: leave out the batched (C4) and served (C5) sub-objects")
     ap.add_argument("--profile-evals", type=int, default=0)
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
                     help="c2 (default, the benchmark line); c1, c3 for the other single workloads; "
@@ -699,8 +776,8 @@ def main():
                                                 "instead of the autotuned shape (profiling commands)")
     ap.add_argument("--requests", type=int, default=48, help="c5: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="c5: mean arrival rate (1/s)")
-    ap.add_argument("--torque-tol", type=float, default=1e-2, help="c5: relax torque tolerance (T)")
-    ap.add_argument("--max-time", type=float, default=20e-12, help="c5: relax max simulated time (s)")
+    ap.add_argument("--torque-tol", type=float, default=1e-4, help="c5: relax torque tolerance (T)")
+    ap.add_argument("--max-time", type=float, default=10e-9, help="c5: relax max simulated time (s)")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="c5: admission budget (GB)")
     ap.add_argument("--attempts", type=int, default=4, help="c5: lock-step attempts between admissions")
     args = ap.parse_args()

@@ -390,6 +390,15 @@ int mmp_batch_profile_read(mmp_batch* b, int pass, long long* launches, double* 
 /* Wait for all work of the context. */
 int mmp_sync(mmp_ctx* ctx);
 
+/* Measured FP32 FMA throughput of the current device (no counterpart in the
+ * paper: the arithmetic ceiling the passes' FP32 rate is reported against).
+ * Runs `reps` launches of a kernel of eight independent FMA chains per
+ * thread at full occupancy on `stream` (cudaStream_t as void*, NULL = the
+ * default stream), each timed with CUDA events; returns the best launch as
+ * GFLOP/s (2 flops per FMA) and its time in ms (may be NULL).  Allocates
+ * and frees 1.2 MB of device memory; synchronises the stream. */
+int mmp_fp32_peak(void* stream, int reps, double* gflops, double* ms_per_launch);
+
 /* Message of the last error on this thread ("" if none). */
 const char* mmp_last_error(void);
 

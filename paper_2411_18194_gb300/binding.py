@@ -92,6 +92,7 @@ _SIGS = {
     "mmp_batch_profile": ([_c.c_void_p, _c.c_int], _c.c_int),
     "mmp_batch_profile_read": ([_c.c_void_p, _c.c_int, _c.POINTER(_c.c_longlong), _c.POINTER(_c.c_double)],
                                _c.c_int),
+    "mmp_fp32_peak": ([_c.c_void_p, _c.c_int, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)], _c.c_int),
 }
 KERNEL_IDS = {"pass_a": 0, "pass_b": 1, "field": 2, "assemble": 3, "strain": 4, "elastic": 5}
 
@@ -176,6 +177,18 @@ def demag_noalloc(shape, cell, M, B, stream=None):
     cx, cy, cz = (float(c) for c in cell)
     _check(library().mmp_demag_noalloc(nx, ny, nz, cx, cy, cz, _ptr(M), _ptr(B), ctypes.c_void_p(handle)))
     return B
+
+
+def fp32_peak(reps=20, stream=None):
+    """Measured FP32 FMA throughput of the current device: (GFLOP/s, ms per
+    launch) of the best of `reps` launches (mmp_fp32_peak)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    _check(library().mmp_fp32_peak(ctypes.c_void_p(handle), int(reps), ctypes.byref(g), ctypes.byref(ms)))
+    return g.value, ms.value
 
 
 class Magnet:

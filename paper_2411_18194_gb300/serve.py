@@ -94,6 +94,12 @@ class Request:
         self.mag = None
         self.bytes = 0
         self.result = None
+        self.sim_time = None          # simulated time at the end of the solve (s)
+
+    @property
+    def time_capped(self):
+        """The solve ended on its simulated-time limit, not on the torque tolerance."""
+        return self.sim_time is not None and self.sim_time >= self.max_time * (1.0 - 1e-9)
 
     @property
     def latency(self):
@@ -159,6 +165,7 @@ class RelaxServer:
             self.batch.remove(req.mag)
             req.done = now
             req.status = status
+            req.sim_time = _sim_time(req.mag)
             if self.keep:
                 req.result = _read_m(req.mag)
             req.mag.close()
@@ -195,6 +202,13 @@ class RelaxServer:
         self.batch.close()
 
 
+def _sim_time(mag):
+    try:
+        return float(mag.time()["t"])
+    except (AttributeError, KeyError, TypeError):
+        return None
+
+
 def _read_m(mag):
     import torch
     nx, ny, nz = mag.shape
@@ -215,6 +229,7 @@ def serve_one_at_a_time(requests, dt0=1e-14, keep_results=False, clock=time.perf
         req.admitted = clock() - t0
         mag = _make_magnet(req.workload, dt0)
         mag.relax(torque_tol=req.torque_tol, max_time=req.max_time)
+        req.sim_time = _sim_time(mag)
         if keep_results:
             req.result = _read_m(mag)
         mag.close()
@@ -227,5 +242,7 @@ def serve_one_at_a_time(requests, dt0=1e-14, keep_results=False, clock=time.perf
 def latency_stats(reqs):
     lat = np.array([r.latency for r in reqs], dtype=np.float64)
     span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    capped = [getattr(r, "time_capped", False) for r in reqs]
     return {"solves": len(reqs), "solves_per_s": len(reqs) / span, "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "span_s": span}
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "span_s": span,
+            "time_capped_fraction": float(np.mean(capped)) if capped else 0.0}
