@@ -155,14 +155,15 @@ def geometry(shape):
 
 
 def traffic_from_profile(kernel):
-    """ncu DRAM bytes per launch recorded for this kernel source, or None if
-    the source changed since the counters were taken."""
+    """ncu DRAM bytes per launch recorded for this kernel's sources, or None
+    if any of them changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[kernel]
-        src = os.path.join(ROOT, "paper_2411_18194_gb300", "csrc", rec["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return rec["dram_bytes_per_launch"] if sha == rec["source_sha"] else None
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2411_18194_gb300", "csrc", f), "rb").read())
+        return rec["dram_bytes_per_launch"] if h.hexdigest()[:16] == rec["source_sha"] else None
     except Exception:
         return None
 
