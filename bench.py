@@ -494,6 +494,49 @@ def batch_measure(args, init):
     return line if rank == 0 else None
 
 
+def pass_b_ms(mag, engine, evals=12):
+    """Mean device time of pass B (CUDA events) over `evals` field evaluations
+    of the magnet's current state with the given engine bits."""
+    mag.set_shape(engine=engine)
+    mag.eval_field(0)
+    mag.eval_field(0)
+    mag.profile(True)
+    for _ in range(evals):
+        mag.eval_field(0)
+    n, ms = mag.profile_read()["pass_b"]
+    mag.profile(False)
+    return ms / n
+
+
+def tensor_core_study(mag_c2):
+    """Pass B with the final DFT32 of its y transforms on the CUDA cores and
+    on the tensor cores (split TF32), on the large ferromagnet and on the
+    largest batched instance (512x512x1, solo context)."""
+    import torch
+    import paper_2411_18194_gb300 as pkg
+    from inputs import Problem, random_unit_vectors
+    out = {}
+    base = mag_c2.get_shape()
+    if not base["engine"] & 1:
+        return None
+    e0 = base["engine"] & ~4
+    out["c2_1024x1024x8"] = {"cuda_cores_ms": pass_b_ms(mag_c2, e0), "tensor_cores_ms": pass_b_ms(mag_c2, e0 | 4)}
+    mag_c2.set_shape(**base)
+    p = Problem((512, 512, 1), (2e-9, 2e-9, 2e-9), 1, frozenset({"DEMAG", "EXCH"}))
+    p.set("MS", 1.4e6).set("AEX", 2e-11).set("ALPHA", 0.5)
+    m = pkg.Magnet.from_problem(p)
+    m.set_m(0, torch.from_numpy(random_unit_vectors(777, p.shape)).cuda())
+    e = m.get_shape()["engine"] & ~4
+    out["batched_512x512x1"] = {"cuda_cores_ms": pass_b_ms(m, e), "tensor_cores_ms": pass_b_ms(m, e | 4)}
+    m.close()
+    for v in out.values():
+        v["tensor_over_cuda"] = v["tensor_cores_ms"] / v["cuda_cores_ms"]
+    out["what"] = ("pass B per launch (CUDA events, mean of 12) with the final length-32 DFT of every y "
+                   "transform on the CUDA cores or as a split-TF32 GEMM on the tensor cores (tcgen05, "
+                   "engine bit 4); the benchmark value uses the autotuned shape")
+    return out
+
+
 # the batched and served halves of the metric as they ride along the default
 # line: their own workloads, compact (bounded run time)
 EXTRA_C4 = {"instances": 256, "steps": 10, "warmup": 3}
@@ -719,6 +762,10 @@ def run_gpu(args):
                                          "thread, %d blocks x 256 threads, %.3f ms each" % (8 * nsm, pk_ms))
         if graph_path:
             line["graph_path"] = graph_path
+    if args.workload == "c2" and not args.no_extras:
+        tcs = tensor_core_study(mag)
+        if rank == 0 and tcs is not None:
+            line["tensor_core_stage"] = tcs
     mag.close()
     del mag
     if args.workload == "c2" and not args.no_extras:

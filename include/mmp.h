@@ -296,10 +296,17 @@ typedef struct mmp_shape {
                           apply to it;
                           MMP_ENGINE_WARP_X: passes A and C on warp-level transforms in
                           tiles of one row pair (Px = 2048, i.e. nx of 769 .. 1024);
-                          ty, tyc and radix_x do not apply to them. */
+                          ty, tyc and radix_x do not apply to them;
+                          MMP_ENGINE_TC_Y (with MMP_ENGINE_WARP_B): the final length-32
+                          DFT of every y transform of pass B as a dense GEMM on the
+                          tensor cores in split TF32 (each product as three TF32
+                          products, FP32 accumulation in tensor memory).  A device-side
+                          wait of it that runs past its limit makes the next
+                          synchronising call return MMP_E_TIMEOUT. */
 } mmp_shape;
 #define MMP_ENGINE_WARP_B 1
 #define MMP_ENGINE_WARP_X 2
+#define MMP_ENGINE_TC_Y 4
 
 /* Current shape of the context (chosen at creation: ty from the grid, the
  * radix-16 plans; the warp passes where they apply (pass B with R = 2 when

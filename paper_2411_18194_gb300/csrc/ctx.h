@@ -47,6 +47,8 @@ struct mmp_ctx {
   float2 *d_tw_x = nullptr, *d_tw_y = nullptr, *d_tw_ly = nullptr, *d_tw_z = nullptr;
   float2* d_tw_wy = nullptr;   // warp pass B twiddles (engine & MMP_ENGINE_WARP_B)
   float2 *d_tw_wx = nullptr, *d_tw_wx2 = nullptr;   // warp passes A and C (MMP_ENGINE_WARP_X)
+  float* d_tw_tc = nullptr;    // tensor-core DFT32 matrices (MMP_ENGINE_TC_Y)
+  unsigned* d_flag = nullptr;  // set by a device wait that ran past its limit
   unsigned* d_red = nullptr;   // [0] error bits, [1] torque bits
   double* d_energy = nullptr;  // [MMP_NTERMS] (mmp_energy)
   unsigned* h_red = nullptr;   // pinned

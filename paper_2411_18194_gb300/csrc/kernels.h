@@ -64,7 +64,10 @@ struct DemagArgs {
   const float2* tw_wy;       // N = Ly (pass B)
   const float2* tw_wx;       // N = Px / 2 (passes A and C)
   const float2* tw_wx2;      // w_Px^x, x < Px / 2 (natural order; passes A and C)
-  int engine;                // pass B: 0 block Stockham passes, 1 warp passes
+  const float* tw_tc;        // tensor-core DFT32 matrices, split TF32 (tcdft.cuh layout)
+  unsigned* err;             // set to 1 by a device wait that ran past its limit
+  int engine;                // pass B: 0 block Stockham passes, 1 warp passes, 2 warp passes with
+                             // the final DFT32 of each y transform on the tensor cores
 };
 
 struct Coefs {
@@ -143,6 +146,8 @@ inline bool passb_w_supported(const Grid& g, int R) {
   if (g.ny > Ly) return false;
   return g.nz == 1 || g.nz == 2 || g.nz == 4 || g.nz == 8;
 }
+// whether the tensor-core DFT32 stage applies on top of the warp pass B
+inline bool passb_tc_supported(const Grid& g, int R) { return passb_w_supported(g, R); }
 cudaError_t launch_field(const Grid& g, const DemagArgs& d, const Coefs& c, const FieldArgs& f,
                          int nsub, bool demag, int threads, cudaStream_t s);
 cudaError_t launch_strain(const Grid& g, const ElasticArgs& e, int nsub, cudaStream_t s);

@@ -91,6 +91,20 @@ int cuda_check(mmp_ctx* c, cudaError_t e, const char* what) {
     if (_rc != MMP_OK) return _rc;                       \
   } while (0)
 
+// A device-side wait that ran past its limit (the tensor-core stage) sets
+// ctx->d_flag; read it at a point that synchronises anyway.
+int check_flag(mmp_ctx* ctx) {
+  if (!(ctx->engine & MMP_ENGINE_TC_Y) || !ctx->d_flag) return MMP_OK;
+  unsigned f = 0;
+  CK(cudaMemcpyAsync(&f, ctx->d_flag, sizeof f, cudaMemcpyDeviceToHost, ctx->stream), "read device flag");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (f) {
+    ctx->poisoned = true;
+    return fail(MMP_E_TIMEOUT, "a device-side wait of the tensor-core stage ran past its limit");
+  }
+  return MMP_OK;
+}
+
 int check_ctx(mmp_ctx* ctx) {
   if (!ctx) return fail(MMP_E_INVAL, "null context");
   if (ctx->poisoned) return fail(MMP_E_STATE, "context poisoned by an earlier CUDA error");
@@ -395,7 +409,11 @@ bool shape_ok(const mmp_ctx* ctx, const mmp_shape& s, const char** why) {
     *why = "pass A or C shared memory above 227 KB";
     return false;
   }
-  if (s.engine & ~(MMP_ENGINE_WARP_B | MMP_ENGINE_WARP_X)) { *why = "unknown engine bits"; return false; }
+  if (s.engine & ~(MMP_ENGINE_WARP_B | MMP_ENGINE_WARP_X | MMP_ENGINE_TC_Y)) { *why = "unknown engine bits"; return false; }
+  if ((s.engine & MMP_ENGINE_TC_Y) && !((s.engine & MMP_ENGINE_WARP_B) && passb_tc_supported(g, s.R))) {
+    *why = "the tensor-core stage needs the warp pass B";
+    return false;
+  }
   if ((s.engine & MMP_ENGINE_WARP_X) && !xw_supported(g)) {
     *why = "the warp passes A and C need Px = 2048 (nx of 769 .. 1024)";
     return false;
@@ -430,6 +448,11 @@ int apply_shape(mmp_ctx* ctx, const mmp_shape& s) {
   TRY(upload_table(ctx, ctx->d_tw_x, pass_twiddles(ctx->plan_x)));
   TRY(upload_table(ctx, ctx->d_tw_ly, pass_twiddles(ctx->plan_ly)));
   if (s.engine & MMP_ENGINE_WARP_B) TRY(upload_table(ctx, ctx->d_tw_wy, warp_twiddles(g.Py / s.R)));
+  if ((s.engine & MMP_ENGINE_TC_Y) && !ctx->d_tw_tc) {
+    const std::vector<float> t = tc_dft32_table();
+    TRY(alloc_into(ctx, ctx->d_tw_tc, t.size() * sizeof(float)));
+    CK(cudaMemcpy(ctx->d_tw_tc, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tensor-core table");
+  }
   if (s.engine & MMP_ENGINE_WARP_X) {
     TRY(upload_table(ctx, ctx->d_tw_wx, warp_twiddles(g.Px / 2)));
     std::vector<float2> w = roots(g.Px);
@@ -485,7 +508,9 @@ DemagArgs demag_args(mmp_ctx* ctx) {
   d.tw_wy = ctx->d_tw_wy;
   d.tw_wx = ctx->d_tw_wx;
   d.tw_wx2 = ctx->d_tw_wx2;
-  d.engine = (ctx->engine & MMP_ENGINE_WARP_B) ? 1 : 0;
+  d.tw_tc = ctx->d_tw_tc;
+  d.err = ctx->d_flag;
+  d.engine = (ctx->engine & MMP_ENGINE_WARP_B) ? ((ctx->engine & MMP_ENGINE_TC_Y) ? 2 : 1) : 0;
   return d;
 }
 
@@ -753,7 +778,7 @@ int advance(mmp_ctx* ctx, long long nsteps, double until, int relax, double torq
     }
   }
   if (!adaptive) CK(cudaStreamSynchronize(ctx->stream), "sync");
-  return MMP_OK;
+  return check_flag(ctx);
 }
 
 // Device time per pass (ms) of `reps` field evaluations of the current
@@ -858,6 +883,9 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
 #define CR(x) do { if (rc == MMP_OK) rc = (x); } while (0)
   CR(alloc_into(ctx, ctx->d_coef, 2 * MMP_MAX_REGIONS * sizeof(RegionCoef)));
   CR(alloc_into(ctx, ctx->d_red, 2 * sizeof(unsigned)));
+  CR(alloc_into(ctx, ctx->d_flag, sizeof(unsigned)));
+  if (rc == MMP_OK && cudaMemset(ctx->d_flag, 0, sizeof(unsigned)) != cudaSuccess)
+    rc = cuda_check(ctx, cudaGetLastError(), "clear device flag");
   if (rc == MMP_OK && cudaMallocHost(&ctx->h_red, 2 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     rc = fail(MMP_E_OOM, "pinned allocation failed");
@@ -907,7 +935,7 @@ int mmp_destroy(mmp_ctx* ctx) {
     if (ev) cudaEventDestroy(ev);
   void* bufs[] = {ctx->d_regions, ctx->d_coef, ctx->d_hA, ctx->d_y, ctx->d_stage, ctx->d_B, ctx->d_eps,
                   ctx->d_sig, ctx->d_T, ctx->d_tw_x, ctx->d_tw_y, ctx->d_tw_ly, ctx->d_tw_z, ctx->d_red,
-                  ctx->d_energy, ctx->d_tw_wy, ctx->d_tw_wx, ctx->d_tw_wx2};
+                  ctx->d_energy, ctx->d_tw_wy, ctx->d_tw_wx, ctx->d_tw_wx2, ctx->d_tw_tc, ctx->d_flag};
   for (void* p : bufs) dfree(ctx, p);
   for (int i = 0; i < 7; ++i) dfree(ctx, ctx->d_k[i]);
   if (ctx->h_red) cudaFreeHost(ctx->h_red);
@@ -1085,7 +1113,7 @@ int mmp_eval_field(mmp_ctx* ctx, int sub, float* B, float* tau) {
     CK(cudaMemcpyAsync(tau, ctx->d_k[0] + sub * n3, n3 * sizeof(float), cudaMemcpyDefault, ctx->stream),
        "copy tau");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
-  return MMP_OK;
+  return check_flag(ctx);
 }
 
 int mmp_step(mmp_ctx* ctx, int nsteps) {
@@ -1299,7 +1327,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
   if (batch) {
     start.R = 1;
     start.stage_kernel = 0;
-    start.engine = 0;
+    start.engine = 0;   // batch members run the block engine
     start.ty = 8;   // the largest tiles that fit
     while (start.ty > 2 && !shape_ok(ctx, start, &why)) start.ty >>= 1;
     if (!shape_ok(ctx, start, &why)) return fail(MMP_E_INVAL, "no batch shape fits this grid: %s", why);
@@ -1338,18 +1366,19 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
         s.R = R;
         s.stage_kernel = st;
         s.radix_y = ry;
-        s.engine &= ~MMP_ENGINE_WARP_B;
+        s.engine &= ~(MMP_ENGINE_WARP_B | MMP_ENGINE_TC_Y);
         if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
       }
-  for (int R : {1, 2}) {
-    if (batch) break;
-    mmp_shape s = start;
-    s.R = R;
-    s.stage_kernel = 0;
-    s.radix_y = 0;
-    s.engine |= MMP_ENGINE_WARP_B;
-    if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
-  }
+  for (int R : {1, 2})
+    for (int tc = 0; tc < 2; ++tc) {
+      if (batch) break;
+      mmp_shape s = start;
+      s.R = R;
+      s.stage_kernel = 0;
+      s.radix_y = 0;
+      s.engine = (s.engine & ~MMP_ENGINE_TC_Y) | MMP_ENGINE_WARP_B | (tc ? MMP_ENGINE_TC_Y : 0);
+      if (shape_ok(ctx, s, &why)) cand_b.push_back(s);
+    }
   // two interleaved rounds; a candidate's time is its better round
   std::vector<double> t_ac(cand_ac.size(), 1e300), t_b(cand_b.size(), 1e300);
   for (int round = 0; round < 2; ++round) {
@@ -1380,7 +1409,8 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
       best.R = cand_b[i].R;
       best.stage_kernel = cand_b[i].stage_kernel;
       best.radix_y = cand_b[i].radix_y;
-      best.engine = (best.engine & ~MMP_ENGINE_WARP_B) | (cand_b[i].engine & MMP_ENGINE_WARP_B);
+      best.engine = (best.engine & ~(MMP_ENGINE_WARP_B | MMP_ENGINE_TC_Y)) |
+                    (cand_b[i].engine & (MMP_ENGINE_WARP_B | MMP_ENGINE_TC_Y));
     }
   // keep the starting shape unless the combination measures faster by > 2 %
   // (longer, interleaved measurement of both)
@@ -1412,7 +1442,7 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms) {
 int mmp_sync(mmp_ctx* ctx) {
   TRY(check_ctx(ctx));
   CK(cudaStreamSynchronize(ctx->stream), "sync");
-  return MMP_OK;
+  return check_flag(ctx);
 }
 
 }  // extern "C"

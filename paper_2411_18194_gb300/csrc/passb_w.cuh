@@ -24,6 +24,7 @@
 #include "kernels.h"
 #include "wfft.cuh"
 #include "copy.cuh"
+#include "tcdft.cuh"
 
 namespace mmp {
 
@@ -34,8 +35,9 @@ namespace mmp {
 // (32 M float2).
 __host__ __device__ __forceinline__ int passb_w_pitch(int M) { return 32 * M + (M < 32 ? 8 : 0); }
 __host__ __device__ __forceinline__ int passb_w_groups(int nz, int M) { return (3 * nz + 32 / M - 1) / (32 / M); }
-__host__ __device__ __forceinline__ size_t passb_w_smem(int nz, int M) {
-  return ((size_t)passb_w_groups(nz, M) * (32 / M) * passb_w_pitch(M) + 32 * M) * sizeof(float2);
+__host__ __device__ __forceinline__ size_t passb_w_smem(int nz, int M, bool tc = false) {
+  return ((size_t)passb_w_groups(nz, M) * (32 / M) * passb_w_pitch(M) + 32 * M) * sizeof(float2) +
+         (tc ? (size_t)4 * kTcB * sizeof(float) + 64 : 0);
 }
 // Warps per CTA of the warp pass B: 12 when there are at least 12 column
 // groups (two per warp at nz = 8, Ly = 1024), else 8.
@@ -196,8 +198,45 @@ __device__ __forceinline__ void prefetch_rows_l2(const float* kplane, const Grid
     prefetch_l2(p, (unsigned)(bytes < 65536 ? bytes : 65536));
 }
 
-// Pass B of plane kx, class r, on NW warps.  M = Ly / 32.
-template <int NZ, int M, int NW>
+// The y transform of one column group: on the warp FFT alone, or (TC) with
+// its stage 1 (the in-register DFT32) as a split-TF32 GEMM on the tensor
+// cores for the whole warpgroup (tcdft.cuh).  The inverse is the conjugate
+// of the forward transform of the conjugate.
+struct TcCtx {
+  uint32_t tbase;   // the CTA's tensor memory
+  const float* Bs;  // the DFT32 matrices (shared memory)
+  uint64_t* mbar;   // per warpgroup
+  uint32_t phase;   // this thread's next phase parity of its warpgroup's mbarrier
+  unsigned* err;
+};
+// `valid` = false: a warp without a column this round (only with TC, where
+// all four warps of a warpgroup take part in its GEMM): it contributes zeros
+// and its results are not used.
+template <int M, bool INV, bool TC>
+__device__ __forceinline__ void ytransform(float2 (&v)[32], float2* scr, const float2* twT, TcCtx& tc,
+                                           bool valid) {
+  if constexpr (!TC) {
+    wfft<M, INV>(v, scr, twT);
+  } else {
+    if (valid) {
+      if (INV) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i].y = -v[i].y;
+      }
+      wfft_head<M>(v, scr, twT);
+    }
+    const int g = threadIdx.x >> 7;
+    tc_stage32(v, tc.tbase, g * kTcCols, tc.Bs, tc.mbar + g, tc.phase, tc.err);
+    if (INV) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i].y = -v[i].y;
+    }
+  }
+}
+
+// Pass B of plane kx, class r, on NW warps.  M = Ly / 32.  TC: the final
+// DFT32 of every y transform on the tensor cores (whole warpgroups).
+template <int NZ, int M, int NW, bool TC = false>
 __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g, const DemagArgs& d, int kx,
                                               int r) {
   constexpr int Ly = 32 * M;
@@ -208,10 +247,29 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
   constexpr int NT = NW * 32;
   const int R = d.R;
   const int ny = g.ny, Py = g.Py;
+  static_assert(!TC || (NW % 4 == 0 && (NW / 4) * kTcCols <= 512), "tensor-core stage: whole warpgroups");
+  constexpr int NRND = (NGRP + NW - 1) / NW;   // column rounds (every warp takes part in each with TC)
   float2* W = reinterpret_cast<float2*>(sraw);
   float2* twT = W + NGRP * B * LP;
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   float2* Tk = d.T + (long long)kx * NCOL * ny;
+  TcCtx tc{0u, nullptr, nullptr, 0u, d.err};
+  if constexpr (TC) {
+    float* Bs = reinterpret_cast<float*>(twT + 32 * M);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + 4 * kTcB);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
+    for (int i = threadIdx.x; i < 4 * kTcB; i += NT) Bs[i] = __ldg(d.tw_tc + i);
+    if (threadIdx.x < NW / 4) mbar_init(mbar + threadIdx.x, 1);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (warp == 0) tmem_alloc(tslot, 512);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    tc.tbase = *tslot;
+    tc.Bs = Bs;
+    tc.mbar = mbar;
+  }
   // 0. the plane into W (asynchronous copies), the zero rows, L2 prefetch of
   // the kernel rows, the warp twiddles
   if ((ny & 1) == 0) {
@@ -242,7 +300,10 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
   cp_async_wait_all();
   __syncthreads();
   // 1. forward y transforms: lane l takes y = l + 32 m of each column of its group
-  for (int grp = warp; grp < NGRP; grp += NW) {
+  for (int rnd = 0; rnd < NRND; ++rnd) {
+    const int grp = warp + rnd * NW;
+    const bool valid = grp < NGRP;
+    if (!TC && !valid) break;
     float2 v[32];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -250,7 +311,7 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const int y = lane + 32 * m;
-        float2 x = col < NCOL ? W[col * LP + y] : make_float2(0.0f, 0.0f);
+        float2 x = valid && col < NCOL ? W[col * LP + y] : make_float2(0.0f, 0.0f);
         if (r) x = cmul(x, __ldg(d.tw_y + r * y));
         v[b * M + m] = x;
       }
@@ -258,10 +319,10 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
     __syncwarp();
     // the transpose scratch: this group's own columns of W (B LP >= 1024 float2)
     float2* scr = W + grp * B * LP;
-    wfft<M, false>(v, scr, twT);
+    ytransform<M, false, TC>(v, scr, twT, tc, valid);
     // lane j: column grp B + j / M, ky' = j mod M + M k2
     const int col = grp * B + lane / M, k1 = lane % M;
-    if (col < NCOL) {
+    if (valid && col < NCOL) {
 #pragma unroll
       for (int k2 = 0; k2 < 32; ++k2) W[col * LP + k1 + M * k2] = v[k2];
     }
@@ -277,20 +338,23 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
   }
   __syncthreads();
   // 3. inverse y transforms
-  for (int grp = warp; grp < NGRP; grp += NW) {
+  for (int rnd = 0; rnd < NRND; ++rnd) {
+    const int grp = warp + rnd * NW;
+    const bool valid = grp < NGRP;
+    if (!TC && !valid) break;
     float2 v[32];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int col = grp * B + b;
 #pragma unroll
       for (int m = 0; m < M; ++m)
-        v[b * M + m] = col < NCOL ? W[col * LP + lane + 32 * m] : make_float2(0.0f, 0.0f);
+        v[b * M + m] = valid && col < NCOL ? W[col * LP + lane + 32 * m] : make_float2(0.0f, 0.0f);
     }
     __syncwarp();
     float2* scr = W + grp * B * LP;
-    wfft<M, true>(v, scr, twT);
+    ytransform<M, true, TC>(v, scr, twT, tc, valid);
     const int col = grp * B + lane / M, k1 = lane % M;
-    if (col < NCOL) {
+    if (valid && col < NCOL) {
       if (R == 1) {
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
@@ -308,6 +372,12 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
       }
     }
     __syncwarp();
+  }
+  if constexpr (TC) {
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (warp == 0) tmem_free(tc.tbase, 512);
   }
   // 4. R = 2: out[y] = h_0[y] + w^(-y) h_1[y], y < ny; this CTA writes its
   // half of y.  Four pairs of values per thread and step, all loads first.
@@ -366,21 +436,21 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
 // ------------------------------------------------------------ kernels ----
 namespace mmp {
 
-template <int NZ, int M>
+template <int NZ, int M, bool TC>
 __global__ void __launch_bounds__(32 * passb_w_warps(NZ, M), 1) k_passB_w(Grid g, DemagArgs d) {
   extern __shared__ __align__(16) unsigned char sraw[];
-  passB_w_plane<NZ, M, passb_w_warps(NZ, M)>(sraw, g, d, blockIdx.y, (int)(blockIdx.x % d.R));
+  passB_w_plane<NZ, M, passb_w_warps(NZ, M), TC>(sraw, g, d, blockIdx.y, (int)(blockIdx.x % d.R));
 }
 
 // One launch over the kx planes: R CTAs per plane (a cluster when R = 2).
-template <int NZ, int M>
+template <int NZ, int M, bool TC>
 cudaError_t launch_passB_w_t(const Grid& g, const DemagArgs& d, cudaStream_t s) {
-  const size_t sm = passb_w_smem(NZ, M);
-  cudaError_t e = cudaFuncSetAttribute(k_passB_w<NZ, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = passb_w_smem(NZ, M, TC);
+  cudaError_t e = cudaFuncSetAttribute(k_passB_w<NZ, M, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int threads = 32 * passb_w_warps(NZ, M);
   if (d.R == 1) {
-    k_passB_w<NZ, M><<<dim3(1, g.kxn), threads, sm, s>>>(g, d);
+    k_passB_w<NZ, M, TC><<<dim3(1, g.kxn), threads, sm, s>>>(g, d);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -395,16 +465,25 @@ cudaError_t launch_passB_w_t(const Grid& g, const DemagArgs& d, cudaStream_t s) 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_passB_w<NZ, M>, g, d);
+  return cudaLaunchKernelEx(&cfg, k_passB_w<NZ, M, TC>, g, d);
 }
 
 template <int M>
 cudaError_t launch_passB_w_m(const Grid& g, const DemagArgs& d, cudaStream_t s) {
+  if (d.engine == 2) {   // the final DFT32 of the y transforms on the tensor cores
+    switch (g.nz) {
+      case 1: return launch_passB_w_t<1, M, true>(g, d, s);
+      case 2: return launch_passB_w_t<2, M, true>(g, d, s);
+      case 4: return launch_passB_w_t<4, M, true>(g, d, s);
+      case 8: return launch_passB_w_t<8, M, true>(g, d, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (g.nz) {
-    case 1: return launch_passB_w_t<1, M>(g, d, s);
-    case 2: return launch_passB_w_t<2, M>(g, d, s);
-    case 4: return launch_passB_w_t<4, M>(g, d, s);
-    case 8: return launch_passB_w_t<8, M>(g, d, s);
+    case 1: return launch_passB_w_t<1, M, false>(g, d, s);
+    case 2: return launch_passB_w_t<2, M, false>(g, d, s);
+    case 4: return launch_passB_w_t<4, M, false>(g, d, s);
+    case 8: return launch_passB_w_t<8, M, false>(g, d, s);
     default: return cudaErrorInvalidValue;
   }
 }

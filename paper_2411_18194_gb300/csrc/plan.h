@@ -2,6 +2,8 @@
 // lengths, radix plans and FP64-built twiddle tables.
 #pragma once
 #include <math.h>
+#include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -109,6 +111,35 @@ inline std::vector<float2> warp_twiddles(int N) {
       w[k1 * 32 + l] = make_float2((float)cos(a), (float)(-sin(a)));
     }
   return w;
+}
+
+// The DFT32 matrices of the tensor-core stage (tcdft.cuh): F = w32^(m k)
+// real and imaginary parts, each split into TF32 hi (round to nearest,
+// ties away) and the FP32 remainder, in the no-swizzle core-matrix layout:
+// element (k, n) at float (8 (n / 8) + k / 4) * 32 + 4 (n % 8) + k % 4 of its
+// 1024-float matrix; order Fr hi, Fr lo, Fi hi, Fi lo.  Built in FP64.
+inline float tf32_round_host(float x) {
+  uint32_t b;
+  memcpy(&b, &x, 4);
+  b = (b + 0x1000u) & ~0x1FFFu;
+  float y;
+  memcpy(&y, &b, 4);
+  return y;
+}
+inline std::vector<float> tc_dft32_table() {
+  std::vector<float> B(4 * 1024);
+  for (int k = 0; k < 32; ++k)
+    for (int n = 0; n < 32; ++n) {
+      const double a = 2.0 * 3.14159265358979323846 * (double)((k * n) % 32) / 32.0;
+      const double fr = cos(a), fi = -sin(a);
+      const int off = (8 * (n / 8) + (k / 4)) * 32 + 4 * (n % 8) + (k % 4);
+      const float frh = tf32_round_host((float)fr), fih = tf32_round_host((float)fi);
+      B[0 * 1024 + off] = frh;
+      B[1 * 1024 + off] = (float)(fr - (double)frh);
+      B[2 * 1024 + off] = fih;
+      B[3 * 1024 + off] = (float)(fi - (double)fih);
+    }
+  return B;
 }
 
 inline std::vector<float2> roots(int P) {

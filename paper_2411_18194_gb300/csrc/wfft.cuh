@@ -104,20 +104,29 @@ __host__ __device__ __forceinline__ int wfft_twiddles(int M) { return 32 * M; }
 // On exit lane j holds v[k2] = X_b[k1 + M k2] with b = j / M, k1 = j mod M.
 // `scr`: the warp's 1024 float2 of shared memory (free on entry; holds
 // nothing on exit).  `twT`: the twiddle table above (shared memory).
+// Stage 1: the in-register DFTs of length M over m.
 template <int M>
-__device__ __forceinline__ void wfft_fwd(float2 (&v)[32], float2* scr, const float2* twT) {
-  constexpr bool INV = false;
+__device__ __forceinline__ void wfft_stage1(float2 (&v)[32]) {
   constexpr int B = 32 / M;
-  const int l = lane_id();
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     float2 t[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) t[m] = v[b * M + m];
-    dft_m<M, INV>(t);
+    dft_m<M, false>(t);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[b * M + m] = t[m];
   }
+}
+
+// Stage 1, twiddles and transpose (forward): on return lane j holds the 32
+// inputs of its final DFT32 (stage 2).
+template <int M>
+__device__ __forceinline__ void wfft_head(float2 (&v)[32], float2* scr, const float2* twT) {
+  constexpr bool INV = false;
+  constexpr int B = 32 / M;
+  const int l = lane_id();
+  wfft_stage1<M>(v);
   if constexpr (M > 1) {
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) {
@@ -134,7 +143,12 @@ __device__ __forceinline__ void wfft_fwd(float2 (&v)[32], float2* scr, const flo
 #pragma unroll
   for (int c = 0; c < 32; ++c) v[c] = scr[l * 32 + (c ^ l)];
   __syncwarp();
-  dft32<INV>(v);
+}
+
+template <int M>
+__device__ __forceinline__ void wfft_fwd(float2 (&v)[32], float2* scr, const float2* twT) {
+  wfft_head<M>(v, scr, twT);
+  dft32<false>(v);
 }
 
 // Forward (INV = false) or inverse (INV = true, exp(+2 pi i k n / N), no
