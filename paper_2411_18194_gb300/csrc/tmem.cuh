@@ -1,11 +1,10 @@
-// tmem.cuh -- tensor memory (TMEM) used as per-thread staging storage.
+// tmem.cuh -- tensor memory (TMEM): allocation, fences and addressing.
 //
 // sm_103a has 256 KB of tensor memory per SM (128 lanes x 512 columns of
-// 32 bits) next to the tensor cores.  The passes that do not run MMAs use
-// it as a per-thread buffer: thread t of warp w owns lane 32 (w mod 4) +
-// (t mod 32), and the warpgroups of a CTA take disjoint column ranges.
-// Data goes in and out through registers (tcgen05.st / tcgen05.ld, 32x32b
-// shape: each thread moves consecutive columns of its own lane).
+// 32 bits) next to the tensor cores.  A warp accesses the lane quarter
+// 32 (w mod 4) .. 32 (w mod 4) + 31 of its warp index w; data moves between
+// a thread's registers and its own lane (tcgen05.st / tcgen05.ld, 32x32b
+// shape), and the MMAs read and write it directly (tcdft.cuh).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -39,48 +38,6 @@ __device__ __forceinline__ uint32_t tmem_addr(uint32_t base, int col) {
   return base + (lane0 << 16) + (uint32_t)col;
 }
 
-// 56 consecutive columns of the thread's lane from v (warp-wide, converged).
-__device__ __forceinline__ void tmem_st56(uint32_t taddr, const float (&v)[56]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0+0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n"
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0+32], {%33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48};\n"
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0+48], {%49, %50, %51, %52, %53, %54, %55, %56};\n"
-      :
-      : "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])), "r"(__float_as_uint(v[32])), "r"(__float_as_uint(v[33])), "r"(__float_as_uint(v[34])), "r"(__float_as_uint(v[35])), "r"(__float_as_uint(v[36])), "r"(__float_as_uint(v[37])), "r"(__float_as_uint(v[38])), "r"(__float_as_uint(v[39])), "r"(__float_as_uint(v[40])), "r"(__float_as_uint(v[41])), "r"(__float_as_uint(v[42])), "r"(__float_as_uint(v[43])), "r"(__float_as_uint(v[44])), "r"(__float_as_uint(v[45])), "r"(__float_as_uint(v[46])), "r"(__float_as_uint(v[47])), "r"(__float_as_uint(v[48])), "r"(__float_as_uint(v[49])), "r"(__float_as_uint(v[50])), "r"(__float_as_uint(v[51])), "r"(__float_as_uint(v[52])), "r"(__float_as_uint(v[53])), "r"(__float_as_uint(v[54])), "r"(__float_as_uint(v[55]))
-      : "memory");
-}
-
-// 30 consecutive columns of the thread's lane into v, waiting for them (one asm
-// statement, so no use of v can be scheduled before the wait).
-__device__ __forceinline__ void tmem_ld30(uint32_t taddr, float (&v)[30]) {
-  uint32_t r[30];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%30+0];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%30+16];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24, %25, %26, %27}, [%30+24];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%28, %29}, [%30+28];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 30; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 24 consecutive columns of the thread's lane into v, waiting for them (one asm
-// statement, so no use of v can be scheduled before the wait).
-__device__ __forceinline__ void tmem_ld24(uint32_t taddr, float (&v)[24]) {
-  uint32_t r[24];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%24+0];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%24+16];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 24; ++i) v[i] = __uint_as_float(r[i]);
-}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
