@@ -120,8 +120,9 @@ __device__ __forceinline__ void wfft_stage1(float2 (&v)[32]) {
 }
 
 // Stage 1, twiddles and transpose (forward): on return lane j holds the 32
-// inputs of its final DFT32 (stage 2).
-template <int M>
+// inputs of its final DFT32 (stage 2).  TWG: twT is in global memory (read
+// through the read-only path), else in shared memory.
+template <int M, bool TWG = false>
 __device__ __forceinline__ void wfft_head(float2 (&v)[32], float2* scr, const float2* twT) {
   constexpr bool INV = false;
   constexpr int B = 32 / M;
@@ -130,7 +131,7 @@ __device__ __forceinline__ void wfft_head(float2 (&v)[32], float2* scr, const fl
   if constexpr (M > 1) {
 #pragma unroll
     for (int k1 = 1; k1 < M; ++k1) {
-      float2 w = twT[k1 * 32 + l];
+      float2 w = TWG ? __ldg(twT + k1 * 32 + l) : twT[k1 * 32 + l];
       if (INV) w.y = -w.y;
 #pragma unroll
       for (int b = 0; b < B; ++b) v[b * M + k1] = cmul(v[b * M + k1], w);
@@ -145,9 +146,9 @@ __device__ __forceinline__ void wfft_head(float2 (&v)[32], float2* scr, const fl
   __syncwarp();
 }
 
-template <int M>
+template <int M, bool TWG = false>
 __device__ __forceinline__ void wfft_fwd(float2 (&v)[32], float2* scr, const float2* twT) {
-  wfft_head<M>(v, scr, twT);
+  wfft_head<M, TWG>(v, scr, twT);
   dft32<false>(v);
 }
 
@@ -156,13 +157,13 @@ __device__ __forceinline__ void wfft_fwd(float2 (&v)[32], float2* scr, const flo
 // forward transform of the conjugate, so one unrolled body serves both
 // (the negations fold into the neighbouring additions and stores); the
 // kernels are large enough for instruction fetch to matter.
-template <int M, bool INV>
+template <int M, bool INV, bool TWG = false>
 __device__ __forceinline__ void wfft(float2 (&v)[32], float2* scr, const float2* twT) {
   if (INV) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i].y = -v[i].y;
   }
-  wfft_fwd<M>(v, scr, twT);
+  wfft_fwd<M, TWG>(v, scr, twT);
   if (INV) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i].y = -v[i].y;

@@ -30,15 +30,15 @@ namespace mmp {
 constexpr int kXwN = 1024;            // transform length N (Px = 2 N)
 constexpr int kXwThreads = 192;       // six warps: (component, parity)
 
-// Shared memory of the warp passes A and C (bytes).
+// Shared memory of the warp passes A and C (bytes), under 50 KB so that four
+// CTAs (24 warps at 80 registers) share an SM; the warp twiddles are read
+// from global memory through L1.
 //   A: Zin [3][N] float2 (reused as the even warps' scratch), odd scratch
-//      [3][N] float2, warp twiddles [N] float2.
+//      [3][N] float2.
 //   C: gathered half spectra [3][N + 1] float4 (reused as the six warps'
-//      scratch, [6][N] float2), warp twiddles [N] float2.
-__host__ __device__ constexpr size_t passa_w_smem() { return (size_t)(6 * kXwN + kXwN) * sizeof(float2); }
-__host__ __device__ constexpr size_t field_w_smem() {
-  return (size_t)3 * (kXwN + 1) * sizeof(float4) + (size_t)kXwN * sizeof(float2);
-}
+//      scratch, [6][N] float2).
+__host__ __device__ constexpr size_t passa_w_smem() { return (size_t)(6 * kXwN) * sizeof(float2); }
+__host__ __device__ constexpr size_t field_w_smem() { return (size_t)3 * (kXwN + 1) * sizeof(float4); }
 
 // ------------------------------------------------------------- pass A ----
 // Stage value of part p, component c at 4 consecutive cells (16-byte loads).
@@ -133,9 +133,8 @@ __device__ __forceinline__ void passA_w_tile(unsigned char* sraw, const Grid& g,
   const int nx = g.nx, ny = g.ny;
   float2* Zin = reinterpret_cast<float2*>(sraw);   // [3][N]; even warps' scratch afterwards
   float2* Sodd = Zin + 3 * N;                      // [3][N] odd warps' scratch
-  float2* twT = Sodd + 3 * N;                      // [N]
+  const float2* twT = d.tw_wx;                     // [N], global (L1)
   const int lane = lane_id(), warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < N; i += kXwThreads) twT[i] = __ldg(d.tw_wx + i);
   // 1. stage assembly of both rows into Zin (zero for x >= nx and a row y >= ny)
   for (int i = threadIdx.x; i < 3 * (N - nx); i += kXwThreads) {
     const int c = i / (N - nx), x = nx + i - c * (N - nx);
@@ -177,7 +176,7 @@ __device__ __forceinline__ void passA_w_tile(unsigned char* sraw, const Grid& g,
   }
   __syncthreads();   // every warp holds its input: Zin becomes the even warps' scratch
   float2* scr = par ? Sodd + c * N : Zin + c * N;
-  wfft<32, false>(v, scr, twT);
+  wfft<32, false, true>(v, scr, twT);
   // lane j: v[k2] = Z[2 k' + par], k' = j + 32 k2; natural order into the scratch
 #pragma unroll
   for (int k2 = 0; k2 < 32; ++k2) scr[lane + 32 * k2] = v[k2];
@@ -209,7 +208,7 @@ __device__ __forceinline__ void field_w_tile(unsigned char* sraw, const Grid& g,
   const int ny = g.ny;
   float4* G = reinterpret_cast<float4*>(sraw);          // [3][N + 1]: (X_a, X_b) of the two rows
   float2* S = reinterpret_cast<float2*>(sraw);          // afterwards [6][N] warp scratch
-  float2* twT = reinterpret_cast<float2*>(G + 3 * (N + 1));
+  const float2* twT = d.tw_wx;                          // [N], global (L1)
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   // 1. gather T[k][c][z][y0 .. y0 + 1], k <= N
   const bool two = y0 + 1 < ny;
@@ -230,7 +229,6 @@ __device__ __forceinline__ void field_w_tile(unsigned char* sraw, const Grid& g,
     }
   }
   cp_async_commit();
-  for (int i = threadIdx.x; i < N; i += kXwThreads) twT[i] = __ldg(d.tw_wx + i);
   cp_async_wait_all();
   __syncthreads();
   // 2. inverse transforms: warp (c, par) takes Z[2 k' + par], k' = l + 32 m,
@@ -246,7 +244,7 @@ __device__ __forceinline__ void field_w_tile(unsigned char* sraw, const Grid& g,
   }
   __syncthreads();   // every warp holds its input: G becomes the warps' scratch
   float2* scr = S + warp * N;
-  wfft<32, true>(v, scr, twT);
+  wfft<32, true, true>(v, scr, twT);
   // lane j: v[k2] = IDFT_N(Z[2 k' + par])[x], x = j + 32 k2
   if (par) {
 #pragma unroll
@@ -274,13 +272,13 @@ __device__ __forceinline__ void field_w_tile(unsigned char* sraw, const Grid& g,
 
 // ------------------------------------------------------------ kernels ----
 template <int NSUB, bool ASSEMBLE>
-__global__ void __launch_bounds__(kXwThreads, 3) k_passA_w(Grid g, StageArgs a, DemagArgs d, Coefs co) {
+__global__ void __launch_bounds__(kXwThreads, 4) k_passA_w(Grid g, StageArgs a, DemagArgs d, Coefs co) {
   extern __shared__ __align__(16) unsigned char sraw[];
   passA_w_tile<NSUB, ASSEMBLE>(sraw, g, a, d, co, blockIdx.y, 2 * blockIdx.x);
 }
 
 template <int NSUB, bool UNI>
-__global__ void __launch_bounds__(kXwThreads, 3) k_field_w(Grid g, DemagArgs d, Coefs co, FieldArgs f) {
+__global__ void __launch_bounds__(kXwThreads, 4) k_field_w(Grid g, DemagArgs d, Coefs co, FieldArgs f) {
   extern __shared__ __align__(16) unsigned char sraw[];
   field_w_tile<NSUB, UNI>(sraw, g, d, co, f, blockIdx.y, 2 * blockIdx.x);
 }
