@@ -126,6 +126,118 @@ __device__ __forceinline__ void passA_w_cells(const Grid& g, const StageArgs& a,
     for (int i = 0; i < V; ++i) Zf[2 * (c * kXwN + x0 + i) + h] = Mv[c][i];
 }
 
+// a.k[j], a.coef[j] for a run-time j by selects (an indexed parameter array
+// would be copied to local memory)
+__device__ __forceinline__ const float* stage_k(const StageArgs& a, int j) {
+  const float* p = a.k[0];
+#pragma unroll
+  for (int i = 1; i < 7; ++i) p = j == i ? a.k[i] : p;
+  return p;
+}
+__device__ __forceinline__ float stage_coef(const StageArgs& a, int j) {
+  float c = a.coef[0];
+#pragma unroll
+  for (int i = 1; i < 7; ++i) c = j == i ? a.coef[i] : c;
+  return c;
+}
+
+// Stage assembly of the tile's two rows with the stage vectors streamed
+// through shared memory (one sublattice, no elastic parts, nx a multiple of
+// 4): y (or the current state) and each previous stage k_j arrive in turn
+// by asynchronous 16-byte copies into two alternating 24 KB buffers (the
+// transforms' space, free until then), so all of a vector's bytes are in
+// flight at once; each thread keeps the sums of its 4-cell items in
+// registers.  Then the renormalisation (last stage), the stage state
+// written once, and M = Ms m into Zin.
+template <bool ASSEMBLE>
+__device__ __forceinline__ void passA_w_assemble_async(float* buf0, float* buf1, float2* Zin, const Grid& g,
+                                                       const StageArgs& a, const Coefs& co, int z, int y0) {
+  constexpr int N = kXwN, IT = 3;   // at most 3 items of 4 cells per thread (2 rows x N / 4 / 192)
+  const int nx = g.nx, ny = g.ny, q = nx >> 2;
+  const long long n = g.n;
+  const int nvec = ASSEMBLE ? 1 + a.nk : 1;
+  const bool two = y0 + 1 < ny;
+  const long long row0 = (long long)nx * (y0 + (long long)ny * z);   // first cell of row y0
+  // copies of vector v: 2 rows x 3 components x q pieces of 16 bytes
+  auto issue = [&](int v, float* b) {
+    const float* src = v == 0 ? (ASSEMBLE ? a.y : a.stage) : stage_k(a, v - 1);
+    const int pieces = (two ? 2 : 1) * 3 * q;
+    for (int e = threadIdx.x; e < pieces; e += kXwThreads) {
+      const int hc = e / q, j = e - hc * q, h = hc / 3, c = hc - 3 * h;
+      cp_async16(b + (h * 3 + c) * nx + 4 * j, src + (long long)c * n + row0 + (long long)h * nx + 4 * j);
+    }
+    cp_async_commit();
+  };
+  float acc[IT][3][4];
+  issue(0, buf0);
+  if (nvec > 1) issue(1, buf1);
+  for (int v = 0; v < nvec; ++v) {
+    if (v + 1 < nvec) cp_async_wait_one();
+    else cp_async_wait_all();
+    __syncthreads();
+    float* b = (v & 1) ? buf1 : buf0;
+    const float cv = v == 0 ? 1.0f : stage_coef(a, v - 1);
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int e = threadIdx.x + it * kXwThreads;
+      if (e >= 2 * q) continue;
+      const int h = e >= q, x0 = 4 * (e - h * q);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4 w = *reinterpret_cast<const float4*>(b + (h * 3 + c) * nx + x0);
+        if (v == 0) {
+          acc[it][c][0] = w.x; acc[it][c][1] = w.y; acc[it][c][2] = w.z; acc[it][c][3] = w.w;
+        } else {
+          acc[it][c][0] = fmaf(cv, w.x, acc[it][c][0]);
+          acc[it][c][1] = fmaf(cv, w.y, acc[it][c][1]);
+          acc[it][c][2] = fmaf(cv, w.z, acc[it][c][2]);
+          acc[it][c][3] = fmaf(cv, w.w, acc[it][c][3]);
+        }
+      }
+    }
+    __syncthreads();   // the buffer is read: it takes vector v + 2
+    if (v + 2 < nvec) issue(v + 2, b);
+  }
+  const float ms_uni = co.uniform ? co.reg[0].ms : 0.0f;
+  float* Zf = reinterpret_cast<float*>(Zin);
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int e = threadIdx.x + it * kXwThreads;
+    if (e >= 2 * q) continue;
+    const int h = e >= q, x0 = 4 * (e - h * q);
+    if (h == 1 && !two) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Zf[2 * (c * N + x0 + i) + h] = 0.0f;
+      continue;
+    }
+    const long long cell0 = row0 + (long long)h * nx + x0;
+    if (ASSEMBLE && a.normalize) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float m0 = acc[it][0][i], m1 = acc[it][1][i], m2 = acc[it][2][i];
+        const float nn = m0 * m0 + m1 * m1 + m2 * m2;
+        const float r = nn > 0.0f ? rnorm3df(m0, m1, m2) : 1.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[it][c][i] *= r;
+      }
+    }
+    if (ASSEMBLE) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        *reinterpret_cast<float4*>(a.stage + (long long)c * n + cell0) =
+            make_float4(acc[it][c][0], acc[it][c][1], acc[it][c][2], acc[it][c][3]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float ms = co.uniform ? ms_uni : co.reg[co.regions[cell0 + i]].ms;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Zf[2 * (c * N + x0 + i) + h] = ms * acc[it][c][i];
+    }
+  }
+}
+
 template <int NSUB, bool ASSEMBLE>
 __device__ __forceinline__ void passA_w_tile(unsigned char* sraw, const Grid& g, const StageArgs& a,
                                              const DemagArgs& d, const Coefs& co, int z, int y0) {
@@ -136,11 +248,10 @@ __device__ __forceinline__ void passA_w_tile(unsigned char* sraw, const Grid& g,
   const float2* twT = d.tw_wx;                     // [N], global (L1)
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   // 1. stage assembly of both rows into Zin (zero for x >= nx and a row y >= ny)
-  for (int i = threadIdx.x; i < 3 * (N - nx); i += kXwThreads) {
-    const int c = i / (N - nx), x = nx + i - c * (N - nx);
-    Zin[c * N + x] = make_float2(0.0f, 0.0f);
-  }
-  if ((nx & 3) == 0) {
+  if (NSUB == 1 && (nx & 3) == 0 && a.nparts == a.nsub) {
+    passA_w_assemble_async<ASSEMBLE>(reinterpret_cast<float*>(Zin), reinterpret_cast<float*>(Sodd), Zin, g, a, co,
+                                     z, y0);
+  } else if ((nx & 3) == 0) {
     const int q = nx >> 2;
     for (int e = threadIdx.x; e < 2 * q; e += kXwThreads) {
       const int h = e >= q, x0 = 4 * (e - h * q), y = y0 + h;
@@ -162,6 +273,10 @@ __device__ __forceinline__ void passA_w_tile(unsigned char* sraw, const Grid& g,
         for (int c = 0; c < 3; ++c) Zf[2 * (c * N + x0) + h] = 0.0f;
       }
     }
+  }
+  for (int i = threadIdx.x; i < 3 * (N - nx); i += kXwThreads) {
+    const int c = i / (N - nx), x = nx + i - c * (N - nx);
+    Zin[c * N + x] = make_float2(0.0f, 0.0f);
   }
   __syncthreads();
   // 2. forward transforms: warp (c, par), lane l takes x = l + 32 m
