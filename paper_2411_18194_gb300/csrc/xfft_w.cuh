@@ -16,7 +16,9 @@
 // shared memory, forward transforms, the half spectra of both rows to T.
 // Pass C: the half spectra of both rows gathered into shared memory with
 // asynchronous copies, inverse transforms, the demag field of the two rows,
-// then the local field and torque of every cell (field_cells).
+// then the local field and torque of every cell: four cells per item with
+// the tile rows of m staged in shared memory (stencil4.cuh), or one cell
+// per thread (field_cells) for two sublattices or several regions.
 #pragma once
 #include "kernels.h"
 #include "wfft.cuh"
@@ -24,6 +26,7 @@
 #include "stage.cuh"
 #include "pass_a.cuh"
 #include "field.cuh"
+#include "stencil4.cuh"
 
 namespace mmp {
 
@@ -381,8 +384,25 @@ __device__ __forceinline__ void field_w_tile(unsigned char* sraw, const Grid& g,
     }
   }
   __syncthreads();
-  // 3. local field and torque of the two rows
-  field_cells<NSUB, true, UNI>(reinterpret_cast<const float*>(S), 4 * N, N, 2, g, co, f, z, y0);
+  // 3. local field and torque of the two rows.  One sublattice of uniform
+  // material with nx a multiple of 4: the tile rows of m into the odd
+  // warps' scratch (free now; component c at floats 4 c N + 2 N) by 16-byte
+  // asynchronous copies, then four cells per item (stencil4.cuh).
+  if (NSUB == 1 && UNI && (g.nx & 3) == 0) {
+    float* Sf = reinterpret_cast<float*>(S);
+    const int nx = g.nx, q = nx >> 2, nrows = two ? 2 : 1;
+    const long long n = g.n, row0 = (long long)nx * (y0 + (long long)ny * z);
+    for (int e = threadIdx.x; e < 3 * nrows * q; e += kXwThreads) {
+      const int c = e / (nrows * q), rem = e - c * nrows * q, h = rem / q, j = rem - h * q;
+      cp_async16(Sf + c * 4 * N + 2 * N + h * N + 4 * j, f.stage + c * n + row0 + (long long)h * nx + 4 * j);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    field_cells4<true>(Sf + 2 * N, Sf, 4 * N, N, nrows, g, co, f, z, y0);
+  } else {
+    field_cells<NSUB, true, UNI>(reinterpret_cast<const float*>(S), 4 * N, N, 2, g, co, f, z, y0);
+  }
 }
 
 // ------------------------------------------------------------ kernels ----

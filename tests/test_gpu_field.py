@@ -113,6 +113,39 @@ def test_warp_x_passes_parity(shape, cell, seed, terms, nreg, empty):
     mag.close()
 
 
+# Pass C's four-cell stencil (one sublattice, uniform material, nx a
+# multiple of 4, tile rows of m staged in shared memory): shape, cell, seed,
+# terms, open boundary.  The DMI ghosts at every x and y edge, the open
+# boundary, a last tile of one row (odd ny), nx = N exactly (the last item
+# has no right neighbour), cubic anisotropy and the magnetoelastic field.
+STENCIL4_CASES = [
+    ((1000, 5, 3), (2e-9, 2e-9, 1e-9), 71, FM, False),
+    ((1000, 6, 2), (3e-9, 2e-9, 1e-9), 72, FM, True),
+    ((1024, 4, 2), (2e-9, 2e-9, 1e-9), 73, ("DEMAG", "EXCH", "CUBIC", "ZEEMAN"), False),
+    ((1024, 3, 1), (2e-9, 3e-9, 2e-9), 74, ("DEMAG", "EXCH", "ANIS", "DMI", "MEL", "ELASTIC"), False),
+]
+
+
+@pytest.mark.parametrize("shape,cell,seed,terms,open_bc", STENCIL4_CASES,
+                         ids=["x".join(map(str, c[0])) + "-%d" % c[2] for c in STENCIL4_CASES])
+def test_warp_x_four_cell_stencil_parity(shape, cell, seed, terms, open_bc):
+    w = config_small(shape, cell, seed, terms=terms)
+    p = w.problem
+    p.open_bc = open_bc
+    u = None
+    if "ELASTIC" in terms:
+        nx, ny, nz = shape
+        u = (np.random.default_rng(seed).normal(size=(3, nz, ny, nx)) * 2e-12).astype(np.float32)
+    mag = make_magnet(p, w.m0, u, None if u is None else np.zeros_like(u))
+    assert mag.get_shape()["engine"] & 2
+    Bg, Tg = gpu_eval(mag, p)
+    Bo, To = oracle_eval(p, w.m0, u)
+    tolB = field_tolerance(p, Bo[0])
+    assert np.all(np.abs(Bg[0] - Bo[0]) <= tolB), np.abs(Bg[0] - Bo[0]).max()
+    assert np.all(np.abs(Tg[0] - To[0]) <= torque_tolerance(p, Bo[0], tolB)), np.abs(Tg[0] - To[0]).max()
+    mag.close()
+
+
 def test_warp_x_two_sublattice_magnetoelastic_parity():
     """The two-sublattice magnetoelastic path on the warp x passes (summed M
     in pass A, both sublattices' local fields in pass C)."""
