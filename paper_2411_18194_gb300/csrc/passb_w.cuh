@@ -329,12 +329,38 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
     __syncwarp();
   }
   __syncthreads();
-  // 2. z stage per ky'
-  for (int kp = threadIdx.x; kp < Ly; kp += NT) {
-    const int ky = R * kp + r;
-    const int iky = ky <= Py / 2 ? ky : Py - ky;
-    const RowsGlobal<NZ> rows(kbase + (long long)iky * g.krow);
-    zstage_w<NZ>(W, LP, kp, rows, ky <= Py / 2 ? 1.0f : -1.0f);
+  // 2. z stage per ky'.  ky and its mirror Py - ky use the same kernel row
+  // (|ky|, the odd components changing sign), so a thread takes such a pair
+  // with one row load: kp and Ly - kp in class 0 (kp = 0 and Ly / 2 are
+  // their own mirrors), kp and Ly - 1 - kp in class 1.  The first NT pairs
+  // go one to a thread, the rest are split into single columns, so that no
+  // thread takes more columns than with one column per thread and round.
+  // (Loading a pair's row before the forward transforms, to hide its
+  // latency, measured slower: its 56 registers spill.)
+  {
+    const int npair = r ? Ly / 2 : Ly / 2 - 1;
+    const int pa = npair < NT ? npair : NT;
+    if (threadIdx.x < pa) {
+      const int kp = r ? threadIdx.x : threadIdx.x + 1, km = (r ? Ly - 1 : Ly) - kp;
+      const int ky = R * kp + r;   // <= Py / 2: its mirror R km + r = Py - ky is above
+      const RowsGlobal<NZ> rows(kbase + (long long)ky * g.krow);
+      zstage_w<NZ>(W, LP, kp, rows, 1.0f);
+      zstage_w<NZ>(W, LP, km, rows, -1.0f);
+    }
+    const int nrest = 2 * (npair - pa) + (r ? 0 : 2);
+    for (int v = threadIdx.x; v < nrest; v += NT) {
+      int kp;
+      if (v < 2 * (npair - pa)) {
+        const int u = pa + (v >> 1), k0 = r ? u : u + 1;
+        kp = (v & 1) ? (r ? Ly - 1 : Ly) - k0 : k0;
+      } else {
+        kp = v == 2 * (npair - pa) ? 0 : Ly / 2;
+      }
+      const int ky = R * kp + r;
+      const int iky = ky <= Py / 2 ? ky : Py - ky;
+      const RowsGlobal<NZ> rows(kbase + (long long)iky * g.krow);
+      zstage_w<NZ>(W, LP, kp, rows, ky <= Py / 2 ? 1.0f : -1.0f);
+    }
   }
   __syncthreads();
   // 3. inverse y transforms
