@@ -198,7 +198,11 @@ class Magnet:
     (device or host) or C-contiguous numpy arrays.
     """
 
-    def __init__(self, shape, cell, n_sub=1, stream=None, torch_allocator=True):
+    def __init__(self, shape, cell, n_sub=1, stream=None, torch_allocator=True, allocator=None):
+        """`allocator`: an object with ctypes callbacks `alloc` (ALLOC_FN) and
+        `free` (FREE_FN) serving the context's device allocations (e.g. one
+        that refuses some, to exercise the MMP_E_OOM paths); default
+        PyTorch's caching allocator (`torch_allocator`), else cudaMalloc."""
         lib = library()
         nx, ny, nz = (int(v) for v in shape)
         self.shape = (nx, ny, nz)
@@ -211,7 +215,10 @@ class Magnet:
         self.stream = stream
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
         alloc_fn, free_fn = ALLOC_FN(), FREE_FN()
-        if torch_allocator:
+        if allocator is not None:
+            self._alloc = allocator
+            alloc_fn, free_fn = allocator.alloc, allocator.free
+        elif torch_allocator:
             self._alloc = _TorchAllocator(torch.cuda.current_device(), stream)
             alloc_fn, free_fn = self._alloc.alloc, self._alloc.free
         ctx = ctypes.c_void_p()

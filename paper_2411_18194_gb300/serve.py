@@ -22,8 +22,17 @@ Memory accounting (bytes, FP32 state), what stays resident:
 A request whose kernel spectrum is not resident also needs the FP64 build
 buffers during its admission (the build synchronises and frees them before
 the request joins), so they count against the budget at admission only.
+
+A new geometry's context (and its kernel spectrum) is built on a worker
+thread, on its own CUDA stream, while the batch keeps advancing the members
+already admitted; the request joins at the first lock step after its build
+has finished.  Requests of the same geometry wait for that build (arrival
+order is kept).  A request may carry a wall-clock deadline (seconds after
+its arrival): past it, the request leaves the queue or the batch with the
+status MMP_E_TIMEOUT.
 """
 import collections
+import concurrent.futures
 import time
 
 import numpy as np
@@ -81,13 +90,19 @@ def request_bytes(shape, spectrum_resident):
     return b
 
 
+MMP_E_TIMEOUT = -5     # status of include/mmp.h: a host-side deadline passed
+MMP_E_CUDA = -3
+
+
 class Request:
-    def __init__(self, rid, workload, arrival, torque_tol, max_time):
+    def __init__(self, rid, workload, arrival, torque_tol, max_time, deadline=None):
         self.id = rid
         self.workload = workload
         self.arrival = float(arrival)
         self.torque_tol = float(torque_tol)
         self.max_time = float(max_time)
+        self.deadline = None if deadline is None else float(deadline)   # wall seconds after arrival
+        self.accepted = None          # left the queue (its build started, or it joined)
         self.admitted = None
         self.done = None
         self.status = None
@@ -105,6 +120,9 @@ class Request:
     def latency(self):
         return None if self.done is None else self.done - self.arrival
 
+    def expired(self, now):
+        return self.deadline is not None and now > self.arrival + self.deadline
+
 
 def _make_magnet(w, dt0):
     import torch
@@ -115,10 +133,22 @@ def _make_magnet(w, dt0):
     return mag
 
 
+def _build_async(w, dt0):
+    """_make_magnet on the worker thread, on a CUDA stream of its own (the
+    context keeps it), finished on the device before it returns."""
+    import torch
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        mag = _make_magnet(w, dt0)
+        side.synchronize()
+    return mag
+
+
 class RelaxServer:
     """Admission by memory budget + continuous batching of relax solves."""
 
-    def __init__(self, budget_bytes=150e9, attempts_per_round=4, dt0=1e-14, keep_results=False):
+    def __init__(self, budget_bytes=150e9, attempts_per_round=4, dt0=1e-14, keep_results=False,
+                 build_async=True):
         self.budget = float(budget_bytes)
         self.attempts = int(attempts_per_round)
         self.dt0 = float(dt0)
@@ -126,10 +156,14 @@ class RelaxServer:
         self.batch = Batch()
         self.queue = collections.deque()
         self.active = []
+        self.pending = []                         # (request, future): contexts being built
+        self.building = {}                        # (shape, cell) -> future of its first context
         self.finished = []
-        self.used = 0.0                           # resident bytes: states + resident spectra
+        self.used = 0.0                           # resident bytes: states + resident spectra (+ builds)
         self.spectra = collections.Counter()      # (shape, cell) -> requests using its spectrum
         self.peak_members = 0
+        self.builds_overlapped = 0                # lock steps run while a build was in flight
+        self._pool = concurrent.futures.ThreadPoolExecutor(max_workers=1) if build_async else None
 
     def submit(self, req):
         self.queue.append(req)
@@ -138,44 +172,93 @@ class RelaxServer:
         p = req.workload.problem
         return (tuple(p.shape), tuple(p.cell))
 
+    def _finish(self, req, now, status):
+        req.done = now
+        req.status = status
+        self.finished.append(req)
+
+    def _join(self, req, now):
+        key = self._key(req)
+        self.spectra[key] += 1
+        self.batch.add(req.mag, "relax", req.torque_tol, req.max_time)
+        req.admitted = now
+        self.active.append(req)
+
     def _admit(self, now):
         while self.queue and self.queue[0].arrival <= now:
             req = self.queue[0]
+            if req.expired(now):                       # never admitted: deadline passed in the queue
+                self.queue.popleft()
+                self._finish(req, now, MMP_E_TIMEOUT)
+                continue
             key, shape = self._key(req), req.workload.problem.shape
+            if key in self.building:
+                break                                  # its spectrum is being built (FIFO)
             new = self.spectra[key] == 0
-            if self.active and self.used + request_bytes(shape, not new) > self.budget:
+            if (self.active or self.pending) and self.used + request_bytes(shape, not new) > self.budget:
                 break                                  # wait for memory (FIFO)
             self.queue.popleft()
-            req.mag = _make_magnet(req.workload, self.dt0)   # builds the spectrum if new (and frees the buffers)
+            req.accepted = now
             req.bytes = state_bytes(shape)
+            if new and self._pool is not None:
+                # build on the worker thread while the batch keeps stepping
+                self.used += req.bytes + spectrum_bytes(shape) + build_bytes(shape)
+                fut = self._pool.submit(_build_async, req.workload, self.dt0)
+                self.building[key] = fut
+                self.pending.append((req, fut))
+                continue
+            req.mag = _make_magnet(req.workload, self.dt0)   # builds the spectrum if new (and frees the buffers)
             self.used += req.bytes + (spectrum_bytes(shape) if new else 0)
-            self.spectra[key] += 1
-            self.batch.add(req.mag, "relax", req.torque_tol, req.max_time)
-            req.admitted = now
-            self.active.append(req)
+            self._join(req, now)
         self.peak_members = max(self.peak_members, len(self.active))
+
+    def _collect(self, now):
+        """Requests whose context build has finished join the batch (in
+        order); a failed build ends its request with the library's status."""
+        while self.pending and self.pending[0][1].done():
+            req, fut = self.pending.pop(0)
+            key, shape = self._key(req), req.workload.problem.shape
+            del self.building[key]
+            self.used -= build_bytes(shape)
+            try:
+                req.mag = fut.result()
+            except Exception as e:                     # noqa: BLE001 - reported as the request's status
+                self.used -= req.bytes + spectrum_bytes(shape)
+                self._finish(req, now, getattr(e, "status", MMP_E_CUDA))
+                continue
+            if req.expired(now):
+                req.mag.close()
+                req.mag = None
+                self.used -= req.bytes + spectrum_bytes(shape)
+                self._finish(req, now, MMP_E_TIMEOUT)
+                continue
+            self._join(req, now)
+        self.peak_members = max(self.peak_members, len(self.active))
+
+    def _release(self, req):
+        req.mag.close()
+        req.mag = None
+        self.used -= req.bytes
+        key = self._key(req)
+        self.spectra[key] -= 1
+        if self.spectra[key] == 0:                     # the library freed the shared spectrum
+            self.used -= spectrum_bytes(req.workload.problem.shape)
 
     def _retire(self, now):
         keep = []
         for req in self.active:
             done, status = self.batch.status(req.mag)
-            if not done:
+            if not done and not req.expired(now):
                 keep.append(req)
                 continue
             self.batch.remove(req.mag)
-            req.done = now
-            req.status = status
             req.sim_time = _sim_time(req.mag)
-            if self.keep:
+            if not done:
+                status = MMP_E_TIMEOUT
+            elif self.keep:
                 req.result = _read_m(req.mag)
-            req.mag.close()
-            req.mag = None
-            self.used -= req.bytes
-            key = self._key(req)
-            self.spectra[key] -= 1
-            if self.spectra[key] == 0:                 # the library freed the shared spectrum
-                self.used -= spectrum_bytes(req.workload.problem.shape)
-            self.finished.append(req)
+            self._release(req)
+            self._finish(req, now, status)
         self.active = keep
 
     def run(self, requests, clock=time.perf_counter):
@@ -184,17 +267,31 @@ class RelaxServer:
         for r in sorted(requests, key=lambda r: r.arrival):
             self.submit(r)
         t0 = clock()
-        while self.queue or self.active:
+        while self.queue or self.active or self.pending:
             now = clock() - t0
+            self._collect(now)
             self._admit(now)
             if not self.active:
-                time.sleep(max(0.0, min(0.01, self.queue[0].arrival - now)))
+                if self.pending:
+                    concurrent.futures.wait([self.pending[0][1]], timeout=0.01)
+                elif self.queue:
+                    time.sleep(max(0.0, min(0.01, self.queue[0].arrival - now)))
                 continue
+            if self.pending:
+                self.builds_overlapped += 1
             self.batch.advance(self.attempts)
             self._retire(clock() - t0)
         return self.finished
 
     def close(self):
+        for req, fut in self.pending:
+            try:
+                fut.result().close()
+            except Exception:                          # noqa: BLE001 - closing anyway
+                pass
+        self.pending = []
+        if self._pool is not None:
+            self._pool.shutdown(wait=True)
         for req in self.active:
             self.batch.remove(req.mag)
             req.mag.close()
