@@ -537,6 +537,40 @@ def tensor_core_study(mag_c2):
     return out
 
 
+def spectrum_build_study():
+    """Cold build of a geometry's demag kernel spectrum (what a server pays
+    to admit a new grid): first field evaluation of a fresh context minus a
+    second one, for the largest served grid and the large ferromagnet's
+    grid (cell sizes not used before, so nothing is cached)."""
+    import time
+    import torch
+    import paper_2411_18194_gb300 as pkg
+    from inputs import Problem, random_unit_vectors
+    out = {}
+    for shape, cell in (((1024, 1024, 4), (4e-9, 4e-9, 2e-9)), ((1024, 1024, 8), (2.000001e-9, 2e-9, 1e-9))):
+        p = Problem(shape, cell, 1, frozenset({"DEMAG", "EXCH"}))
+        p.set("MS", 8e5).set("AEX", 1.3e-11).set("ALPHA", 0.5)
+        m = pkg.Magnet.from_problem(p)
+        m.set_m(0, torch.from_numpy(random_unit_vectors(31, shape)).cuda())
+        nx, ny, nz = shape
+        B = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+        T = torch.empty_like(B)
+        t = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m.eval_field(0, B, T)
+            torch.cuda.synchronize()
+            t.append(time.perf_counter() - t0)
+        m.close()
+        out["%dx%dx%d" % shape] = {"cold_ms": round(1e3 * (t[0] - t[1]), 2), "first_eval_ms": round(1e3 * t[0], 2),
+                                   "warm_eval_ms": round(1e3 * t[1], 3)}
+    out["what"] = ("demag kernel spectrum built on the device: Newell (FP64) below the cutoff, the far-field "
+                   "expansion in FP32 above it, FP64 FFTs along axes of padded length >= 64; cold_ms = first "
+                   "field evaluation of a new geometry minus the second")
+    return out
+
+
 # the batched and served halves of the metric as they ride along the default
 # line: their own workloads, compact (bounded run time)
 EXTRA_C4 = {"instances": 256, "steps": 10, "warmup": 3}
@@ -766,6 +800,9 @@ def run_gpu(args):
         tcs = tensor_core_study(mag)
         if rank == 0 and tcs is not None:
             line["tensor_core_stage"] = tcs
+        sbs = spectrum_build_study()
+        if rank == 0:
+            line["demag_spectrum_build"] = sbs
     mag.close()
     del mag
     if args.workload == "c2" and not args.no_extras:
