@@ -57,7 +57,11 @@ enum mmp_status {
     MMP_E_CUDA = -3,       /* a CUDA call failed; the context is poisoned */
     MMP_E_NONFINITE = -4,  /* a NaN/Inf appeared; the step was rolled back */
     MMP_E_TIMEOUT = -5,    /* a host-side deadline passed */
-    MMP_E_STATE = -6       /* context poisoned or call out of order */
+    MMP_E_STATE = -6,      /* context poisoned or call out of order */
+    MMP_E_BOUNDS = -7      /* bounds-checked build only (compiled with -DMMP_CHECK_BOUNDS, loaded
+                            * by the binding when MMP_CHECK_BOUNDS=1): a kernel's index check
+                            * found an access outside its buffer (the access was skipped); the
+                            * context is poisoned */
 };
 
 /* Per-sublattice, per-region scalar parameters (mmp_set_param). */

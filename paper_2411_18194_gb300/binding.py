@@ -12,7 +12,12 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "_lib", "libmmp.so")
+# MMP_CHECK_BOUNDS=1 loads the bounds-checked debug build (build.py
+# build(checked=True)): every kernel index check armed, MMP_E_BOUNDS on a
+# failed one.  It is a debugging aid, slower, never the default.
+_CHECKED = os.environ.get("MMP_CHECK_BOUNDS", "") == "1"
+_LIB_PATH = (os.path.join(_HERE, "_lib", "checked", "libmmp_checked.so") if _CHECKED
+             else os.path.join(_HERE, "_lib", "libmmp.so"))
 
 TERM_BITS = {"DEMAG": 1, "EXCH": 2, "ANIS": 4, "DMI": 8, "ZEEMAN": 16, "AFM": 32, "MEL": 64,
              "ELASTIC": 128, "CUBIC": 256}
@@ -21,7 +26,7 @@ PARAM_IDS = {"MS": 0, "AEX": 1, "ALPHA": 2, "KU1": 3, "KU2": 4, "KB1": 5, "DIND"
 PARAM3_IDS = {"ANIS_U": 0, "ANIS_UB": 1, "B_EXT": 2, "ANIS_C1": 3, "ANIS_C2": 4}
 GLOBAL_IDS = {"A0": 0, "A12": 1, "LATTICE_A": 2, "C11": 3, "C12": 4, "C44": 5, "RHO": 6, "ETA": 7}
 STATUS = {0: "MMP_OK", -1: "MMP_E_INVAL", -2: "MMP_E_OOM", -3: "MMP_E_CUDA", -4: "MMP_E_NONFINITE",
-          -5: "MMP_E_TIMEOUT", -6: "MMP_E_STATE"}
+          -5: "MMP_E_TIMEOUT", -6: "MMP_E_STATE", -7: "MMP_E_BOUNDS"}
 
 GOALS = {"steps": 0, "run": 1, "relax": 2}
 METHODS = {"DP45": 0, "HEUN": 1, "BS23": 2, "CASHKARP": 3, "RKF45": 4}
@@ -108,8 +113,9 @@ def library():
     global _lib
     if _lib is None:
         if not os.path.exists(_LIB_PATH):
-            raise RuntimeError("libmmp.so not found at %s: build it with "
-                               "`python -c 'import __graft_entry__ as g; g.build()'`" % _LIB_PATH)
+            raise RuntimeError("%s not found: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+                               " (the bounds-checked one with `python -m paper_2411_18194_gb300.build "
+                               "--checked`)" % _LIB_PATH)
         lib = ctypes.CDLL(_LIB_PATH)
         for name, (args, res) in _SIGS.items():
             fn = getattr(lib, name)

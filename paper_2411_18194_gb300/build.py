@@ -20,6 +20,7 @@ ROOT = os.path.dirname(PKG)
 SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libmmp.so")
+CHECKED_LIB = os.path.join(OUT, "checked", "libmmp_checked.so")
 SOURCES = ["mmp.cu", "pass_a.cu", "pass_b.cu", "field.cu", "elastic.cu", "tensor.cu", "noalloc.cu", "batch.cu", "batch_a.cu", "batch_b.cu", "batch_c.cu", "energy.cu", "passb_w8.cu", "passb_w16.cu", "passb_w32.cu", "passa_w.cu", "field_w.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SPILL_LIMIT = 1024   # bytes of spill stores per thread
@@ -47,14 +48,28 @@ def check_spills(ptxas_out):
     return bad
 
 
-def build(verbose=False, extra=()):
-    os.makedirs(OUT, exist_ok=True)
+def compile_command(src, obj, checked=False, extra=()):
+    """nvcc command of one translation unit (the bounds-checked build adds
+    -DMMP_CHECK_BOUNDS)."""
+    cmd = [nvcc(), "-c", os.path.join(SRC, src), "-o", obj] + ARCH + FLAGS + ["-Xptxas", "-v"] + list(extra)
+    if checked:
+        cmd.append("-DMMP_CHECK_BOUNDS")
+    return cmd
+
+
+def build(verbose=False, extra=(), checked=False):
+    """Compile every translation unit and link the library: libmmp.so, or
+    with `checked` the bounds-checked debug build _lib/checked/libmmp_checked.so
+    (every kernel index check armed; its spills are not limited)."""
+    out = os.path.join(OUT, "checked") if checked else OUT
+    lib_path = CHECKED_LIB if checked else LIB
+    os.makedirs(out, exist_ok=True)
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        obj = os.path.join(out, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc(), "-c", os.path.join(SRC, src), "-o", obj] + ARCH + FLAGS + ["-Xptxas", "-v"] + list(extra)
+        cmd = compile_command(src, obj, checked, extra)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
     failed, spills = [], []
     for cmd, p in procs:
@@ -63,19 +78,20 @@ def build(verbose=False, extra=()):
             sys.stdout.write(out)
         if p.returncode != 0:
             failed.append(" ".join(cmd))
-        spills += check_spills(out)
+        if not checked:
+            spills += check_spills(out)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     if spills:
         raise RuntimeError("kernels spill more than %d bytes:\n" % SPILL_LIMIT + "\n".join(spills))
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     link = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, checked="--checked" in sys.argv))

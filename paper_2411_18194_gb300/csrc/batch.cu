@@ -479,6 +479,15 @@ int mmp_batch_status(mmp_batch* b, mmp_ctx* ctx, int* done, int* status) {
     if (m.ctx == ctx) {
       if (done) *done = member_done(m) ? 1 : 0;
       if (status) *status = m.status;
+#ifdef MMP_CHECK_BOUNDS
+      // the member's index checks report into its context's flag word
+      if (status && ctx->d_flag) {
+        unsigned f = 0;
+        BCK(cudaStreamSynchronize(b->stream), "batch: sync");
+        BCK(cudaMemcpy(&f, ctx->d_flag, sizeof f, cudaMemcpyDeviceToHost), "batch: read flag");
+        if (f & 2u) *status = MMP_E_BOUNDS;
+      }
+#endif
       return MMP_OK;
     }
   return berr(MMP_E_INVAL, "context not in the batch");

@@ -51,7 +51,7 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
   const long long n = g.n;
   const float* ms = f.stage + (long long)3 * s * n;
   const RegionCoef& R = coef_at<UNI>(co, s, reg);
-  if (R.ms == 0.0f) {
+  if (R.ms == 0.0f || !MMP_IN(g, (long long)(3 * s + 2) * n + cell, g.lim_state)) {
     for (int i = 0; i < 3; ++i) { o.B[i] = 0.0f; o.tau[i] = 0.0f; }
     o.mxb = 0.0f;
     return o;
@@ -69,7 +69,7 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
     for (int d = -1; d <= 1; d += 2) {
-      const bool inside = (unsigned)(coord[a] + d) < (unsigned)ext[a];
+      const bool inside = (unsigned)(coord[a] + d) < (unsigned)ext[a] && MMP_IN(g, cell + d * stride[a], n);
       const long long nc = cell + d * stride[a];
       int rn = reg;
       bool present = inside;
@@ -151,7 +151,7 @@ __device__ __forceinline__ CellOut cell_field(const Grid& g, const Coefs& co, co
       for (int a = 0; a < 3; ++a) {
 #pragma unroll
         for (int d = -1; d <= 1; d += 2) {
-          const bool inside = (unsigned)(coord[a] + d) < (unsigned)ext[a];
+          const bool inside = (unsigned)(coord[a] + d) < (unsigned)ext[a] && MMP_IN(g, cell + d * stride[a], n);
           if (!inside) continue;
           const long long nc = cell + d * stride[a];
           if (!UNI && co.reg[so * MMP_MAX_REGIONS + co.regions[nc]].ms == 0.0f) continue;
@@ -217,10 +217,11 @@ __device__ __forceinline__ void inverse_x_components(int c0, int nc, float2* fbu
       const int k = r >> npsh, p = r & (np - 1);
       const int kk = k <= Px / 2 ? k : Px - k;
       const int ya = y0 + 2 * p, yb = ya + 1;
-      const float2* Tc = d.T + (((long long)kk * 3 + c0 + cc) * g.nz + z) * ny;
+      const long long tb = (((long long)kk * 3 + c0 + cc) * g.nz + z) * ny;
+      const float2* Tc = d.T + tb;
       const bool ok = e < total;
-      va[u] = ok && ya < ny ? __ldcg(Tc + ya) : make_float2(0.0f, 0.0f);
-      vb[u] = ok && yb < ny ? __ldcg(Tc + yb) : make_float2(0.0f, 0.0f);
+      va[u] = ok && ya < ny && MMP_IN(g, tb + ya, g.lim_T) ? __ldcg(Tc + ya) : make_float2(0.0f, 0.0f);
+      vb[u] = ok && yb < ny && MMP_IN(g, tb + yb, g.lim_T) ? __ldcg(Tc + yb) : make_float2(0.0f, 0.0f);
     }
 #pragma unroll
     for (int u = 0; u < FU; ++u) {
@@ -258,6 +259,7 @@ __device__ __forceinline__ void field_cells(const float* bd, int cstride, int rs
     int row = e / nx, x = e - row * nx, y = y0 + row;
     if (y >= ny) continue;
     long long cell = x + (long long)nx * (y + (long long)ny * z);
+    if (!MMP_IN(g, cell, g.n)) continue;
     int reg = UNI ? 0 : co.regions[cell];
     float b3[3] = {0.0f, 0.0f, 0.0f};
     if (DEMAG) {
@@ -270,6 +272,7 @@ __device__ __forceinline__ void field_cells(const float* bd, int cstride, int rs
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         long long idx = (long long)(3 * s + i) * n + cell;
+        if (!MMP_IN(g, idx, g.lim_B)) continue;
         f.kout[idx] = o.tau[i];
         if (f.Bout) f.Bout[idx] = o.B[i];
         if (f.err) {

@@ -35,7 +35,30 @@ struct Grid {
   int xbc;              // components per x-FFT call of pass C: 3 or 1
   float h[3];           // cell size (m)
   float ih[3];          // 1 / h
+  // bounds-checked build (MMP_CHECK_BOUNDS): the word the index checks set
+  // (null: not checked) and the element counts they check against
+  unsigned* chk;
+  long long lim_state;  // floats of a state-shaped vector (y, k_j, stage, derivative): 3 parts n
+  long long lim_B;      // floats of B_eff: 3 nsub n
+  long long lim_T;      // complex elements of the spectrum T: kxn 3 nz ny
+  long long lim_khat;   // floats of the kernel octant: kxn kyn krow
 };
+
+// Index checks of the bounds-checked build (compiled with -DMMP_CHECK_BOUNDS):
+// an access whose element index falls outside its buffer is skipped and
+// bit 1 of the context's flag word set, which the host reports as
+// MMP_E_BOUNDS after the call.  In the normal build MMP_IN is `true` and
+// the checks vanish.
+#ifdef MMP_CHECK_BOUNDS
+__device__ __forceinline__ bool in_bounds(const Grid& g, long long i, long long lim) {
+  if (!g.chk || (i >= 0 && i < lim)) return true;
+  atomicOr(g.chk, 2u);
+  return false;
+}
+#define MMP_IN(g, i, lim) (::mmp::in_bounds((g), (long long)(i), (long long)(lim)))
+#else
+#define MMP_IN(g, i, lim) true
+#endif
 
 // State layout: one float vector per RK quantity,
 //   [sub 0: m (3n)] [sub 1: m (3n)] [u (3n)] [v (3n)]   (u, v with elastic)

@@ -93,11 +93,22 @@ int cuda_check(mmp_ctx* c, cudaError_t e, const char* what) {
 
 // A device-side wait that ran past its limit (the tensor-core stage) sets
 // ctx->d_flag; read it at a point that synchronises anyway.
+// The device flag word: bit 0 set by a device-side wait that ran past its
+// limit (tensor-core stage), bit 1 by an index check of the bounds-checked
+// build (MMP_CHECK_BOUNDS).
 int check_flag(mmp_ctx* ctx) {
+#ifdef MMP_CHECK_BOUNDS
+  if (!ctx->d_flag) return MMP_OK;
+#else
   if (!(ctx->engine & MMP_ENGINE_TC_Y) || !ctx->d_flag) return MMP_OK;
+#endif
   unsigned f = 0;
   CK(cudaMemcpyAsync(&f, ctx->d_flag, sizeof f, cudaMemcpyDeviceToHost, ctx->stream), "read device flag");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (f & 2u) {
+    ctx->poisoned = true;
+    return fail(MMP_E_BOUNDS, "bounds-checked build: a kernel index fell outside its buffer (the access was skipped)");
+  }
   if (f) {
     ctx->poisoned = true;
     return fail(MMP_E_TIMEOUT, "a device-side wait of the tensor-core stage ran past its limit");
@@ -135,6 +146,7 @@ int ensure_state(mmp_ctx* ctx) {
   ctx->d_y = ny;
   ctx->nparts = want;
   ctx->nstate = nstate;
+  ctx->g.lim_state = nstate;
   TRY(alloc_into(ctx, ctx->d_stage, nstate * sizeof(float)));
   for (int i = 0; i < 7; ++i) TRY(alloc_into(ctx, ctx->d_k[i], nstate * sizeof(float)));
   ctx->k1_valid = false;
@@ -886,6 +898,12 @@ int mmp_create(mmp_ctx** out, int nx, int ny, int nz, double cx, double cy, doub
   CR(alloc_into(ctx, ctx->d_flag, sizeof(unsigned)));
   if (rc == MMP_OK && cudaMemset(ctx->d_flag, 0, sizeof(unsigned)) != cudaSuccess)
     rc = cuda_check(ctx, cudaGetLastError(), "clear device flag");
+  // sizes the index checks of the bounds-checked build compare against
+  g.chk = ctx->d_flag;
+  g.lim_state = 3LL * nsub * n;
+  g.lim_B = 3LL * nsub * n;
+  g.lim_T = (long long)g.kxn * 3 * g.nz * g.ny;
+  g.lim_khat = (long long)g.kxn * g.kyn * g.krow;
   if (rc == MMP_OK && cudaMallocHost(&ctx->h_red, 2 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     rc = fail(MMP_E_OOM, "pinned allocation failed");

@@ -14,7 +14,7 @@ namespace mmp {
 __global__ void k_assemble(Grid g, StageArgs a) {
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.n;
        cell += (long long)gridDim.x * blockDim.x)
-    assemble_cell(a, g.n, cell);
+    assemble_cell(g, a, g.n, cell);
 }
 
 __global__ void k_normalize(float* m, long long n) {

@@ -27,8 +27,10 @@ __host__ __device__ __forceinline__ size_t passa_inv_offset(int Px, int ty, int 
 // Stage value of component c of part p at a cell: assembled from y and the
 // previous stages (ASSEMBLE) or read from the given stage state.
 template <bool ASSEMBLE>
-__device__ __forceinline__ float stage_value(const StageArgs& a, long long n, int p, int c, long long cell) {
+__device__ __forceinline__ float stage_value(const Grid& g, const StageArgs& a, long long n, int p, int c,
+                                             long long cell) {
   const long long idx = (long long)(3 * p + c) * n + cell;
+  if (!MMP_IN(g, idx, g.lim_state)) return 0.0f;
   if (!ASSEMBLE) return a.stage[idx];
   float acc = a.y[idx];
 #pragma unroll
@@ -79,7 +81,7 @@ __device__ __forceinline__ void passA_components(int c0, int nc, float2* fbuf, c
         const bool ok = e < total && x < nx && y < ny;
         cl[u][h] = ok ? x + (long long)nx * (y + (long long)ny * z) : -1;
 #pragma unroll
-        for (int s = 0; s < NSUB; ++s) mv[u][h][s] = ok ? stage_value<ASSEMBLE>(a, n, s, c, cl[u][h]) : 0.0f;
+        for (int s = 0; s < NSUB; ++s) mv[u][h][s] = ok ? stage_value<ASSEMBLE>(g, a, n, s, c, cl[u][h]) : 0.0f;
       }
     }
 #pragma unroll
@@ -101,7 +103,7 @@ __device__ __forceinline__ void passA_components(int c0, int nc, float2* fbuf, c
           float m = mv[u][h][s];
           if (ASSEMBLE) {
             if (a.normalize) m *= inv[(s * g.ty + row) * nx + x];
-            a.stage[(long long)(3 * s + c) * n + cell] = m;
+            if (MMP_IN(g, (long long)(3 * s + c) * n + cell, g.lim_state)) a.stage[(long long)(3 * s + c) * n + cell] = m;
           }
           v2[h] = fmaf(co.reg[s * MMP_MAX_REGIONS + reg].ms, m, v2[h]);
         }
@@ -124,7 +126,8 @@ __device__ __forceinline__ void passA_components(int c0, int nc, float2* fbuf, c
     float2 X;
     if ((row & 1) == 0) X = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
     else X = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
-    d.T[(((long long)k * 3 + c0 + cc) * g.nz + z) * ny + y] = X;
+    const long long ti = (((long long)k * 3 + c0 + cc) * g.nz + z) * ny + y;
+    if (MMP_IN(g, ti, g.lim_T)) d.T[ti] = X;
   }
   __syncthreads();
 }
@@ -148,16 +151,19 @@ __device__ __forceinline__ void passA_tile(unsigned char* sraw, const Grid& g, c
       if (a.normalize) {
         // 1/|m_i| of the renormalised stage, per sublattice
         for (int s = 0; s < NSUB; ++s) {
-          float v0 = stage_value<true>(a, n, s, 0, cell);
-          float v1 = stage_value<true>(a, n, s, 1, cell);
-          float v2 = stage_value<true>(a, n, s, 2, cell);
+          float v0 = stage_value<true>(g, a, n, s, 0, cell);
+          float v1 = stage_value<true>(g, a, n, s, 1, cell);
+          float v2 = stage_value<true>(g, a, n, s, 2, cell);
           float nn = v0 * v0 + v1 * v1 + v2 * v2;
           inv[(s * g.ty + row) * nx + x] = nn > 0.0f ? rnorm3df(v0, v1, v2) : 1.0f;
         }
       }
       // elastic parts (u, v): assembled here, not transformed
       for (int p = a.nsub; p < a.nparts; ++p)
-        for (int c = 0; c < 3; ++c) a.stage[(long long)(3 * p + c) * n + cell] = stage_value<true>(a, n, p, c, cell);
+        for (int c = 0; c < 3; ++c) {
+          const long long idx = (long long)(3 * p + c) * n + cell;
+          if (MMP_IN(g, idx, g.lim_state)) a.stage[idx] = stage_value<true>(g, a, n, p, c, cell);
+        }
     }
   }
   __syncthreads();

@@ -155,7 +155,7 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
     const float rny = 1.0f / (float)ny;   // e / ny by the exact FP32 quotient (e < 2^22)
     for (int e = threadIdx.x; e < ncol * ny; e += blockDim.x) {
       const int col = (int)(((float)e + 0.5f) * rny), j = e - col * ny;
-      cp_async8(W + fidx(col, j, pitch), Tk + e);
+      if (MMP_IN(g, (long long)kx * ncol * ny + e, g.lim_T)) cp_async8(W + fidx(col, j, pitch), Tk + e);
     }
     cp_async_commit();
   }
@@ -168,6 +168,7 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
       int iky = ky <= Py / 2 ? ky : Py - ky;
       const float4* src = reinterpret_cast<const float4*>(kbase + (long long)iky * krow);
       float4* dst = reinterpret_cast<float4*>(Ks + kp * krow);
+      if (!MMP_IN(g, ((long long)kx * g.kyn + iky) * krow + krow - 1, g.lim_khat)) continue;
       for (int w = 0; w < (krow >> 2); ++w) cp_async16(dst + w, src + w);
     }
     cp_async_commit();
@@ -206,7 +207,10 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
       float2 acc[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        acc[u] = (col0 + u < ncol && j < ny) ? __ldcg(Tk + (long long)(col0 + u) * ny + j) : make_float2(0.0f, 0.0f);
+        acc[u] = (col0 + u < ncol && j < ny &&
+                  MMP_IN(g, (long long)kx * ncol * ny + (long long)(col0 + u) * ny + j, g.lim_T))
+                     ? __ldcg(Tk + (long long)(col0 + u) * ny + j)
+                     : make_float2(0.0f, 0.0f);
       int tq = 0;
       for (int y = j + Ly; y < ny; y += Ly) {
         tq += r;
@@ -215,7 +219,9 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
         float2 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          v[u] = col0 + u < ncol ? __ldcg(Tk + (long long)(col0 + u) * ny + y) : make_float2(0.0f, 0.0f);
+          v[u] = col0 + u < ncol && MMP_IN(g, (long long)kx * ncol * ny + (long long)(col0 + u) * ny + y, g.lim_T)
+                     ? __ldcg(Tk + (long long)(col0 + u) * ny + y)
+                     : make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u] = cadd(acc[u], cmul(v[u], ph));
       }
@@ -239,7 +245,8 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
   if constexpr (NZ == 1) {
     for (int kp = threadIdx.x; kp < Ly; kp += blockDim.x) {
       int ky = R * kp + r;
-      const int iky = ky <= Py / 2 ? ky : Py - ky;
+      int iky = ky <= Py / 2 ? ky : Py - ky;
+      if (!KS && !MMP_IN(g, ((long long)kx * g.kyn + iky) * krow + krow - 1, g.lim_khat)) iky = 0;
       zkz_single<!KS>(W, pitch, kp, Kb + (long long)(KS ? kp : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f);
     }
   } else if constexpr (NZ > 1) {
@@ -248,14 +255,16 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
       int kp = base + (threadIdx.x >> 1);
       bool valid = kp < Ly;
       int ky = valid ? R * kp + r : r;
-      const int iky = ky <= Py / 2 ? ky : Py - ky;
+      int iky = ky <= Py / 2 ? ky : Py - ky;
+      if (!KS && !MMP_IN(g, ((long long)kx * g.kyn + iky) * krow + krow - 1, g.lim_khat)) iky = 0;
       zkz_pair<NZ, !KS>(W, pitch, valid ? kp : 0, valid, threadIdx.x & 1,
                    Kb + (long long)(KS ? (valid ? kp : 0) : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f, d.tw_z);
     }
   } else {
     for (int kp = threadIdx.x; kp < Ly; kp += blockDim.x) {
       int ky = R * kp + r;
-      const int iky = ky <= Py / 2 ? ky : Py - ky;
+      int iky = ky <= Py / 2 ? ky : Py - ky;
+      if (!KS && !MMP_IN(g, ((long long)kx * g.kyn + iky) * krow + krow - 1, g.lim_khat)) iky = 0;
       zkz_generic<!KS>(W, kp, pitch, nz, g.Pz, Kb + (long long)(KS ? kp : iky) * krow, ky <= Py / 2 ? 1.0f : -1.0f,
                   d.tw_z);
     }
@@ -267,7 +276,7 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
   if (R == 1) {
     for (int e = threadIdx.x; e < ncol * ny; e += blockDim.x) {
       int col = e / ny, y = e - col * ny;
-      Tk[e] = W[fidx(col, y, pitch)];
+      if (MMP_IN(g, (long long)kx * ncol * ny + e, g.lim_T)) Tk[e] = W[fidx(col, y, pitch)];
     }
   } else {
     cg::cluster_group cl = cg::this_cluster();
@@ -297,7 +306,8 @@ __device__ __forceinline__ void passB_plane(unsigned char* sraw, const Grid& g, 
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (col0 + u < ncol) Tk[(long long)(col0 + u) * ny + y] = acc[u];
+          if (col0 + u < ncol && MMP_IN(g, (long long)kx * ncol * ny + (long long)(col0 + u) * ny + y, g.lim_T))
+            Tk[(long long)(col0 + u) * ny + y] = acc[u];
       }
     }
     cl.sync();

@@ -277,13 +277,14 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
     const float rq = 1.0f / (float)q;      // e / q by the exact FP32 quotient (e < 2^22)
     for (int e = threadIdx.x; e < NCOL * q; e += NT) {
       const int col = (int)(((float)e + 0.5f) * rq), j = e - col * q;
-      cp_async16(W + col * LP + 2 * j, Tk + (long long)col * ny + 2 * j);
+      const long long ti = (long long)kx * NCOL * ny + (long long)col * ny + 2 * j;
+      if (MMP_IN(g, ti + 1, g.lim_T)) cp_async16(W + col * LP + 2 * j, Tk + (long long)col * ny + 2 * j);
     }
   } else {
     const float rny = 1.0f / (float)ny;
     for (int e = threadIdx.x; e < NCOL * ny; e += NT) {
       const int col = (int)(((float)e + 0.5f) * rny), j = e - col * ny;
-      cp_async8(W + col * LP + j, Tk + e);
+      if (MMP_IN(g, (long long)kx * NCOL * ny + e, g.lim_T)) cp_async8(W + col * LP + j, Tk + e);
     }
   }
   cp_async_commit();
@@ -343,7 +344,8 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
     if (threadIdx.x < pa) {
       const int kp = r ? threadIdx.x : threadIdx.x + 1, km = (r ? Ly - 1 : Ly) - kp;
       const int ky = R * kp + r;   // <= Py / 2: its mirror R km + r = Py - ky is above
-      const RowsGlobal<NZ> rows(kbase + (long long)ky * g.krow);
+      const long long ki = ((long long)kx * g.kyn + ky) * g.krow;
+      const RowsGlobal<NZ> rows(kbase + (MMP_IN(g, ki + g.krow - 1, g.lim_khat) ? (long long)ky * g.krow : 0));
       zstage_w<NZ>(W, LP, kp, rows, 1.0f);
       zstage_w<NZ>(W, LP, km, rows, -1.0f);
     }
@@ -358,7 +360,8 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
       }
       const int ky = R * kp + r;
       const int iky = ky <= Py / 2 ? ky : Py - ky;
-      const RowsGlobal<NZ> rows(kbase + (long long)iky * g.krow);
+      const long long ki = ((long long)kx * g.kyn + iky) * g.krow;
+      const RowsGlobal<NZ> rows(kbase + (MMP_IN(g, ki + g.krow - 1, g.lim_khat) ? (long long)iky * g.krow : 0));
       zstage_w<NZ>(W, LP, kp, rows, ky <= Py / 2 ? 1.0f : -1.0f);
     }
   }
@@ -385,7 +388,8 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
           const int y = k1 + M * k2;
-          if (y < ny) Tk[(long long)col * ny + y] = v[k2];
+          if (y < ny && MMP_IN(g, (long long)kx * NCOL * ny + (long long)col * ny + y, g.lim_T))
+            Tk[(long long)col * ny + y] = v[k2];
         }
       } else {
 #pragma unroll
@@ -436,6 +440,7 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
           const int e = e0 + u * NT;
           const int col = (int)(((float)e + 0.5f) * rcp), y = ylo + 2 * (e - col * cp);
           const float4 s4 = make_float4(a[u].x + b[u].x, a[u].y + b[u].y, a[u].z + b[u].z, a[u].w + b[u].w);
+          if (!MMP_IN(g, (long long)kx * NCOL * ny + (long long)col * ny + y + 1, g.lim_T)) continue;
           float2* dst = Tk + (long long)col * ny + y;
           if ((ny & 1) == 0) {
             *reinterpret_cast<float4*>(dst) = s4;
@@ -450,7 +455,7 @@ __device__ __forceinline__ void passB_w_plane(unsigned char* sraw, const Grid& g
       for (int e = threadIdx.x; e < NCOL * cnt; e += NT) {
         const int col = (int)(((float)e + 0.5f) * rcnt), y = ylo + e - col * cnt;
         const float2 a = W[col * LP + y], b = Wo[col * LP + y];
-        Tk[(long long)col * ny + y] = cadd(a, b);
+        if (MMP_IN(g, (long long)kx * NCOL * ny + (long long)col * ny + y, g.lim_T)) Tk[(long long)col * ny + y] = cadd(a, b);
       }
     }
     cl.sync();

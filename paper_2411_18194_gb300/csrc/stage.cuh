@@ -5,12 +5,13 @@
 
 namespace mmp {
 
-__device__ __forceinline__ void assemble_cell(const StageArgs& a, long long n, long long cell) {
+__device__ __forceinline__ void assemble_cell(const Grid& g, const StageArgs& a, long long n, long long cell) {
   for (int p = 0; p < a.nparts; ++p) {
     float v[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       long long idx = (long long)(3 * p + c) * n + cell;
+      if (!MMP_IN(g, idx, g.lim_state)) { v[c] = 0.0f; continue; }
       float acc = a.y[idx];
 #pragma unroll
       for (int j = 0; j < 7; ++j)
@@ -25,7 +26,10 @@ __device__ __forceinline__ void assemble_cell(const StageArgs& a, long long n, l
       }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) a.stage[(long long)(3 * p + c) * n + cell] = v[c];
+    for (int c = 0; c < 3; ++c) {
+      const long long idx = (long long)(3 * p + c) * n + cell;
+      if (MMP_IN(g, idx, g.lim_state)) a.stage[idx] = v[c];
+    }
   }
 }
 

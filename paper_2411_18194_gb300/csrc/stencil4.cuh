@@ -95,6 +95,7 @@ __device__ __forceinline__ void st4_item(const float* msm, const float* bd, int 
   const unsigned terms = f.terms;
   const bool EX = terms & 2u, DM = terms & 8u, OPEN = terms & kTermOpenBC;
   if (R.ms == 0.0f) {   // empty material: no field, no torque
+    if (!MMP_IN(g, cell0 + 3, n)) return;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const long long idx = (long long)i * n + cell0;
@@ -109,6 +110,9 @@ __device__ __forceinline__ void st4_item(const float* msm, const float* bd, int 
   }
   const bool hasL = x0 > 0, hasR = x0 + 4 < nx, hasYm = y > 0, hasYp = y + 1 < ny;
   const bool hasZm = z > 0, hasZp = z + 1 < g.nz;
+  if (!MMP_IN(g, cell0 + 3, n) || (hasYm && !MMP_IN(g, cell0 - nx, n)) || (hasYp && !MMP_IN(g, cell0 + nx + 3, n)) ||
+      (hasZm && !MMP_IN(g, cell0 - pl, n)) || (hasZp && !MMP_IN(g, cell0 + pl + 3, n)))
+    return;
   // a missing x or y neighbour: the ghost (DMI, closed boundary) or m itself
   // (no DMI, or open boundary, where it also drops out of the DMI sum)
   const bool GH = DM && !OPEN;

@@ -46,8 +46,10 @@ __host__ __device__ constexpr size_t field_w_smem() { return (size_t)3 * (kXwN +
 // ------------------------------------------------------------- pass A ----
 // Stage value of part p, component c at 4 consecutive cells (16-byte loads).
 template <bool ASSEMBLE>
-__device__ __forceinline__ float4 stage_value4(const StageArgs& a, long long n, int p, int c, long long cell) {
+__device__ __forceinline__ float4 stage_value4(const Grid& g, const StageArgs& a, long long n, int p, int c,
+                                               long long cell) {
   const long long idx = (long long)(3 * p + c) * n + cell;
+  if (!MMP_IN(g, idx + 3, g.lim_state)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (!ASSEMBLE) return *reinterpret_cast<const float4*>(a.stage + idx);
   float4 acc = __ldcs(reinterpret_cast<const float4*>(a.y + idx));
 #pragma unroll
@@ -81,10 +83,10 @@ __device__ __forceinline__ void passA_w_cells(const Grid& g, const StageArgs& a,
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       if constexpr (V == 4) {
-        const float4 q = stage_value4<ASSEMBLE>(a, n, s, c, cell0);
+        const float4 q = stage_value4<ASSEMBLE>(g, a, n, s, c, cell0);
         m[c][0] = q.x; m[c][1] = q.y; m[c][2] = q.z; m[c][3] = q.w;
       } else {
-        m[c][0] = stage_value<ASSEMBLE>(a, n, s, c, cell0);
+        m[c][0] = stage_value<ASSEMBLE>(g, a, n, s, c, cell0);
       }
     }
     if (ASSEMBLE && a.normalize) {
@@ -99,7 +101,9 @@ __device__ __forceinline__ void passA_w_cells(const Grid& g, const StageArgs& a,
     if (ASSEMBLE) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        float* dst = a.stage + (long long)(3 * s + c) * n + cell0;
+        const long long idx = (long long)(3 * s + c) * n + cell0;
+        if (!MMP_IN(g, idx + V - 1, g.lim_state)) continue;
+        float* dst = a.stage + idx;
         if constexpr (V == 4) *reinterpret_cast<float4*>(dst) = make_float4(m[c][0], m[c][1], m[c][2], m[c][3]);
         else dst[0] = m[c][0];
       }
@@ -117,9 +121,11 @@ __device__ __forceinline__ void passA_w_cells(const Grid& g, const StageArgs& a,
     for (int p = a.nsub; p < a.nparts; ++p)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        float* dst = a.stage + (long long)(3 * p + c) * n + cell0;
-        if constexpr (V == 4) *reinterpret_cast<float4*>(dst) = stage_value4<true>(a, n, p, c, cell0);
-        else dst[0] = stage_value<true>(a, n, p, c, cell0);
+        const long long idx = (long long)(3 * p + c) * n + cell0;
+        if (!MMP_IN(g, idx + V - 1, g.lim_state)) continue;
+        float* dst = a.stage + idx;
+        if constexpr (V == 4) *reinterpret_cast<float4*>(dst) = stage_value4<true>(g, a, n, p, c, cell0);
+        else dst[0] = stage_value<true>(g, a, n, p, c, cell0);
       }
   }
   float* Zf = reinterpret_cast<float*>(Zin);
@@ -167,7 +173,8 @@ __device__ __forceinline__ void passA_w_assemble_async(float* buf0, float* buf1,
     const int pieces = (two ? 2 : 1) * 3 * q;
     for (int e = threadIdx.x; e < pieces; e += kXwThreads) {
       const int hc = e / q, j = e - hc * q, h = hc / 3, c = hc - 3 * h;
-      cp_async16(b + (h * 3 + c) * nx + 4 * j, src + (long long)c * n + row0 + (long long)h * nx + 4 * j);
+      const long long si = (long long)c * n + row0 + (long long)h * nx + 4 * j;
+      if (MMP_IN(g, si + 3, g.lim_state)) cp_async16(b + (h * 3 + c) * nx + 4 * j, src + si);
     }
     cp_async_commit();
   };
@@ -229,8 +236,9 @@ __device__ __forceinline__ void passA_w_assemble_async(float* buf0, float* buf1,
     if (ASSEMBLE) {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        *reinterpret_cast<float4*>(a.stage + (long long)c * n + cell0) =
-            make_float4(acc[it][c][0], acc[it][c][1], acc[it][c][2], acc[it][c][3]);
+        if (MMP_IN(g, (long long)c * n + cell0 + 3, g.lim_state))
+          *reinterpret_cast<float4*>(a.stage + (long long)c * n + cell0) =
+              make_float4(acc[it][c][0], acc[it][c][1], acc[it][c][2], acc[it][c][3]);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -308,7 +316,9 @@ __device__ __forceinline__ void passA_w_tile(unsigned char* sraw, const Grid& g,
     const float2 A = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
     const float2 Bv = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
     const int k = 2 * kp + par;
-    float2* dst = d.T + (((long long)k * 3 + c) * g.nz + z) * ny + y0;
+    const long long ti = (((long long)k * 3 + c) * g.nz + z) * ny + y0;
+    if (!MMP_IN(g, ti + (two ? 1 : 0), g.lim_T)) continue;
+    float2* dst = d.T + ti;
     if (two && (ny & 1) == 0) {
       *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, Bv.x, Bv.y);
     } else {
@@ -335,12 +345,15 @@ __device__ __forceinline__ void field_w_tile(unsigned char* sraw, const Grid& g,
   if (two && (ny & 1) == 0) {
     for (int e = threadIdx.x; e < 3 * (N + 1); e += kXwThreads) {
       const int c = e / (N + 1), k = e - c * (N + 1);
-      cp_async16(G + e, T0 + k * kstride + c * cstride);
+      const long long ti = (long long)z * ny + y0 + k * kstride + c * cstride;
+      if (MMP_IN(g, ti + 1, g.lim_T)) cp_async16(G + e, T0 + k * kstride + c * cstride);
     }
   } else {
     for (int e = threadIdx.x; e < 3 * (N + 1); e += kXwThreads) {
       const int c = e / (N + 1), k = e - c * (N + 1);
       const float2* src = T0 + k * kstride + c * cstride;
+      const long long ti = (long long)z * ny + y0 + k * kstride + c * cstride;
+      if (!MMP_IN(g, ti + (two ? 1 : 0), g.lim_T)) continue;
       cp_async8(reinterpret_cast<float2*>(G + e), src);
       if (two) cp_async8(reinterpret_cast<float2*>(G + e) + 1, src + 1);
       else reinterpret_cast<float2*>(G + e)[1] = make_float2(0.0f, 0.0f);
@@ -394,7 +407,8 @@ __device__ __forceinline__ void field_w_tile(unsigned char* sraw, const Grid& g,
     const long long n = g.n, row0 = (long long)nx * (y0 + (long long)ny * z);
     for (int e = threadIdx.x; e < 3 * nrows * q; e += kXwThreads) {
       const int c = e / (nrows * q), rem = e - c * nrows * q, h = rem / q, j = rem - h * q;
-      cp_async16(Sf + c * 4 * N + 2 * N + h * N + 4 * j, f.stage + c * n + row0 + (long long)h * nx + 4 * j);
+      const long long si = c * n + row0 + (long long)h * nx + 4 * j;
+      if (MMP_IN(g, si + 3, g.lim_state)) cp_async16(Sf + c * 4 * N + 2 * N + h * N + 4 * j, f.stage + si);
     }
     cp_async_commit();
     cp_async_wait_all();

@@ -69,6 +69,9 @@ def test_binding_ids_match_header_enums():
         assert enums["MMP_GOAL_" + name.upper()] == v
     for name, v in binding.BOUNDARIES.items():
         assert enums["MMP_BC_" + name.upper()] == v
+    for v, name in binding.STATUS.items():
+        if v:
+            assert enums[name] == v
 
 
 def test_create_rejects_bad_arguments_before_touching_the_device():
