@@ -87,9 +87,8 @@ __device__ __forceinline__ float st4_ghost(int i, int a, float d, float g, float
 // its second row.
 template <bool DEMAG>
 __device__ __forceinline__ void st4_item(const float* msm, const float* bd, int cs, int rs, int h, int x0, bool two,
-                                         const Grid& g, const Coefs& co, const FieldArgs& f, int z, int y,
+                                         const Grid& g, const RegionCoef& R, const FieldArgs& f, int z, int y,
                                          long long cell0, float& emax, float& tmax) {
-  const RegionCoef& R = co.reg[0];
   const int nx = g.nx, ny = g.ny;
   const long long n = g.n, pl = (long long)nx * ny;
   const unsigned terms = f.terms;
@@ -269,11 +268,20 @@ template <bool DEMAG>
 __device__ __forceinline__ void field_cells4(const float* msm, const float* bd, int cs, int rs, int nrows,
                                              const Grid& g, const Coefs& co, const FieldArgs& f, int z, int y0) {
   const int nx = g.nx, q = nx >> 2;
+  // the material's coefficients in shared memory: read there, they are not
+  // reloaded from global memory after every store of the outputs
+  __shared__ RegionCoef sR;
+  {
+    const int* src = reinterpret_cast<const int*>(co.reg);
+    int* dst = reinterpret_cast<int*>(&sR);
+    for (int i = threadIdx.x; i < (int)(sizeof(RegionCoef) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
   float emax = 0.0f, tmax = 0.0f;
   for (int e = threadIdx.x; e < nrows * q; e += blockDim.x) {
     const int h = e >= q, x0 = 4 * (e - h * q), y = y0 + h;
     const long long cell0 = x0 + (long long)nx * (y + (long long)g.ny * z);
-    st4_item<DEMAG>(msm, bd, cs, rs, h, x0, nrows == 2, g, co, f, z, y, cell0, emax, tmax);
+    st4_item<DEMAG>(msm, bd, cs, rs, h, x0, nrows == 2, g, sR, f, z, y, cell0, emax, tmax);
   }
   if (f.err) {
     float v = block_max(isnan(emax) ? __int_as_float(0x7f800000) : emax);
