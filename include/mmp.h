@@ -353,9 +353,13 @@ int mmp_autotune(mmp_ctx* ctx, int flags, mmp_shape* chosen, double* eval_ms);
  * mmp_step / mmp_run / mmp_relax on the same context with the same shape.
  *
  * Members: one sublattice, one region (no region map), the demag term on,
- * no AFM / magnetoelastic / elastic terms, shape R = 1, stage_kernel = 0 and
- * engine = 0 (mmp_set_shape or mmp_autotune with MMP_TUNE_BATCH first); otherwise
- * MMP_E_INVAL.  The batch borrows its members: while a context is a member
+ * no AFM / magnetoelastic / elastic terms, and either the shape R = 1,
+ * stage_kernel = 0, engine = 0 (mmp_set_shape or mmp_autotune with
+ * MMP_TUNE_BATCH first; such members share work-list launches), or the warp
+ * passes MMP_ENGINE_WARP_B | MMP_ENGINE_WARP_X with Py / R = 1024 and
+ * stage_kernel = 0 (the creation default of grids with nx of 769 .. 1024 and
+ * ny of 385 .. 512 or 769 .. 1024; such a member gets one launch per pass of
+ * its own); otherwise MMP_E_INVAL.  The batch borrows its members: while a context is a member
  * it must not be used elsewhere, and it must be removed before it is
  * destroyed.  Between mmp_batch_advance calls every member's state sits in
  * its context as usual (mmp_get_m, mmp_get_time work).  All work runs on

@@ -21,7 +21,7 @@ SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libmmp.so")
 CHECKED_LIB = os.path.join(OUT, "checked", "libmmp_checked.so")
-SOURCES = ["mmp.cu", "pass_a.cu", "pass_b.cu", "field.cu", "elastic.cu", "tensor.cu", "noalloc.cu", "batch.cu", "batch_a.cu", "batch_b.cu", "batch_c.cu", "energy.cu", "passb_w8.cu", "passb_w16.cu", "passb_w32.cu", "passa_w.cu", "field_w.cu", "peak.cu"]
+SOURCES = ["mmp.cu", "pass_a.cu", "pass_b.cu", "field.cu", "elastic.cu", "tensor.cu", "noalloc.cu", "batch.cu", "batch_a.cu", "batch_b.cu", "batch_c.cu", "energy.cu", "passb_w8.cu", "passb_w16.cu", "passb_w32.cu", "passa_w.cu", "field_w.cu", "peak.cu", "batch_w.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SPILL_LIMIT = 1024   # bytes of spill stores per thread
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),

@@ -89,6 +89,9 @@ struct Launch {
   int kind, group, threads;
   int off, cnt;
   size_t smem;
+  int warp = -1;   // >= 0: the warp-engine launch of this pass for descriptor `warp`
+  Grid g{};        // its grid
+  int R = 1;       // its ky classes (pass B)
 };
 
 struct ListSet {
@@ -162,6 +165,12 @@ int grow_buf(T*& p, size_t& cap, size_t need) {
   return MMP_OK;
 }
 
+// A member that runs the warp passes A, B and C (its shape: engine 3 with
+// Py / R = 1024, no staged kernel rows), one launch per pass of its own.
+bool warp_member(const mmp_ctx* c) {
+  return c->engine == (MMP_ENGINE_WARP_B | MMP_ENGINE_WARP_X) && c->ks == 0 && batch_warp_supported(c->g, c->R);
+}
+
 bool eligible(const mmp_ctx* c, const char** why) {
   if (c->nsub != 1) { *why = "batch members have one sublattice"; return false; }
   if (!c->uniform) { *why = "batch members have one region"; return false; }
@@ -170,11 +179,13 @@ bool eligible(const mmp_ctx* c, const char** why) {
     *why = "batch members have no AFM, magnetoelastic or elastic term";
     return false;
   }
+  if (c->method != MMP_DP45) { *why = "batch members use the Dormand-Prince solver"; return false; }
+  if (warp_member(c)) return true;
   if (c->R != 1 || c->ks != 0 || c->engine != 0) {
-    *why = "batch members use the shape R = 1, stage_kernel = 0, engine = 0";
+    *why = "batch members use the shape R = 1, stage_kernel = 0, engine = 0, or the warp passes A, B and C "
+           "with Py / R = 1024";
     return false;
   }
-  if (c->method != MMP_DP45) { *why = "batch members use the Dormand-Prince solver"; return false; }
   const Grid& g = c->g;
   if ((long long)g.xb * (g.ty / 2) * g.Px > (long long)fft_cap_a(c->plan_x) * kBatchThreads ||
       (long long)g.xbc * (g.tyc / 2) * g.Px > (long long)fft_cap(c->plan_x) * kBatchThreads ||
@@ -207,6 +218,14 @@ BatchInst make_inst(const Member& m, unsigned* red, double h, int relax) {
   I.d.plan_ly = c->plan_ly;
   I.d.R = 1;
   I.d.ks = 0;
+  if (warp_member(c)) {   // the warp passes' tables and ky classes
+    I.d.R = c->R;
+    I.d.tw_wy = c->d_tw_wy;
+    I.d.tw_wx = c->d_tw_wx;
+    I.d.tw_wx2 = c->d_tw_wx2;
+    I.d.err = c->d_flag;
+    I.d.engine = 1;
+  }
   I.co.reg = c->d_coef;
   I.co.regions = nullptr;
   I.co.hA = nullptr;
@@ -233,9 +252,21 @@ int build_list(mmp_batch* b, const std::vector<int>& mem) {
   L.members = mem;
   std::map<std::tuple<int, int, int>, std::vector<std::pair<double, BatchItem>>> sec;
   std::map<std::tuple<int, int, int>, size_t> smem;
+  std::vector<Launch> warp;   // the warp-engine members' launches
   for (int k = 0; k < (int)mem.size(); ++k) {
     const mmp_ctx* c = b->members[mem[k]].ctx;
     const Grid& g = c->g;
+    if (warp_member(c)) {
+      for (int kind = 0; kind < 3; ++kind) {
+        Launch l{};
+        l.kind = kind;
+        l.warp = k;
+        l.g = g;
+        l.R = c->R;
+        warp.push_back(l);
+      }
+      continue;
+    }
     const int tiles = (g.ny + g.ty - 1) / g.ty;       // pass A
     const int tiles_c = (g.ny + g.tyc - 1) / g.tyc;   // pass C
     const auto ka = std::make_tuple(0, 0, thread_class(c->thrA));
@@ -264,6 +295,8 @@ int build_list(mmp_batch* b, const std::vector<int>& mem) {
     for (auto& e : v) items.push_back(e.second);
     L.launches.push_back(l);
   }
+  for (const Launch& l : warp) L.launches.push_back(l);
+  if (!warp.empty()) BCK(batch_warp_prepare(), "batch: warp-pass attributes");
   L.total = (int)items.size();
   BTRY(grow_buf(b->d_items, b->cap_items, items.size()));
   BTRY(grow_buf(b->d_inst, b->cap_inst, mem.size()));
@@ -315,6 +348,7 @@ struct BTraced {
 };
 
 cudaError_t launch_one(mmp_batch* b, const Launch& l, int stage, cudaStream_t s) {
+  if (l.warp >= 0) return launch_batch_warp(l.kind, b->d_inst, l.warp, l.g, l.R, stage, s);
   const BatchItem* it = b->d_items + l.off;
   if (l.kind == 0) return launch_batch_passA(b->d_inst, it, l.cnt, stage, l.threads, l.smem, s);
   if (l.kind == 1) return launch_batch_passB(l.group, b->d_inst, it, l.cnt, l.threads, l.smem, s);

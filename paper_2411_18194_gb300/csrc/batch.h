@@ -48,6 +48,13 @@ cudaError_t launch_batch_passB(int nz_group, const BatchInst* insts, const Batch
 cudaError_t launch_batch_field(const BatchInst* insts, const BatchItem* items, int nitems, int stage, int threads,
                                size_t smem, cudaStream_t s);
 cudaError_t launch_batch_accept(BatchInst* insts, int n, cudaStream_t s);
+// Warp-engine members (batch_w.cu): passes A and C on row-pair tiles
+// (Px = 2048), pass B on warp transforms of folded y length Py / R = 1024;
+// one launch per pass (`kind` 0 = A, 1 = B, 2 = C) and member `inst`.
+bool batch_warp_supported(const Grid& g, int R);
+cudaError_t batch_warp_prepare();   // shared-memory attributes (outside graph capture)
+cudaError_t launch_batch_warp(int kind, const BatchInst* insts, int inst, const Grid& g, int R, int stage,
+                              cudaStream_t s);
 
 // Stage and field arguments of item descriptor `I` at stage `stage`
 // (built by one thread into shared memory).

@@ -129,7 +129,12 @@ def _make_magnet(w, dt0):
     mag = Magnet.from_problem(w.problem)
     mag.set_m(0, torch.from_numpy(np.ascontiguousarray(w.m0[0])).cuda())
     mag.set_solver(adaptive=True, dt=dt0, tol=w.tol, dt_min=w.dt_min, dt_max=w.dt_max)
-    mag.autotune(batch=True)          # cached per geometry: the batch shape
+    sh = mag.get_shape()
+    ny = w.problem.shape[1]
+    if not (sh["engine"] == 3 and _nice(ny) // sh["R"] == 1024):
+        mag.autotune(batch=True)      # cached per geometry: the batch shape (block engine)
+    # else: the warp passes A, B and C (Px = 2048, folded y length 1024), which a
+    # batch member runs with launches of its own
     return mag
 
 

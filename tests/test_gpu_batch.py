@@ -199,3 +199,51 @@ def test_open_boundary_member_bitwise_equal_to_solo():
     assert not np.array_equal(_m(batched), _m(neumann))
     for x in runs:
         x.close()
+
+
+def test_warp_engine_members_bitwise_equal_to_solo():
+    """Members whose shape runs the warp passes A, B and C (Px = 2048, folded
+    y length 1024: one with R = 1, one with a two-CTA cluster per plane)
+    get their own launches beside the work lists of block-engine members;
+    fixed steps and an adaptive relax are bitwise those of the same
+    contexts alone."""
+    import paper_2411_18194_gb300 as pkg
+    shapes = [(1000, 500, 1), (1000, 900, 1), (64, 48, 2)]
+    for goal in ("steps", "relax"):
+        mags, solo = [], []
+        for i, sh in enumerate(shapes):
+            p = _problem(i, sh, ("DEMAG", "EXCH", "ZEEMAN"))
+            m0 = random_unit_vectors(9100 + i, sh)
+            pair = []
+            for _ in range(2):
+                mag = make_magnet(p, [m0])
+                if sh[0] < 769:
+                    mag.set_shape(R=1, stage_kernel=0, engine=0)
+                else:
+                    assert mag.get_shape()["engine"] == 3, mag.get_shape()
+                if goal == "steps":
+                    mag.set_solver(adaptive=False, dt=_dt(p))
+                else:
+                    mag.set_solver(adaptive=True, dt=1e-14)
+                pair.append(mag)
+            mags.append(pair[0])
+            solo.append(pair[1])
+        with pkg.Batch() as b:
+            for mag in mags:
+                if goal == "steps":
+                    b.add(mag, "steps", 6)
+                else:
+                    b.add(mag, "relax", 1e-3, 2e-12)
+            while b.advance(4):
+                pass
+            for mag in mags:
+                assert b.status(mag)[1] == 0
+        for mag, s in zip(mags, solo):
+            if goal == "steps":
+                s.step(6)
+            else:
+                s.relax(torque_tol=1e-3, max_time=2e-12)
+            assert np.array_equal(_m(mag), _m(s)), (goal, mag.shape)
+            assert mag.time()["t"] == s.time()["t"] and mag.time()["steps"] == s.time()["steps"]
+        for x in mags + solo:
+            x.close()
