@@ -6,7 +6,6 @@
 // ping-pong parity changes inside fixed-step graphs.  One launch per pass
 // and such member, beside the work-list launches of the other members.
 #include "batch.h"
-#include "launch.cuh"
 #include "xfft_w.cuh"
 #include "passb_w.cuh"
 
