@@ -182,9 +182,10 @@ def reduce_over_ranks(maxes, sums, device):
     return mx.tolist(), sm.tolist()
 
 
-def cpu_baseline(seconds=15.0):
-    """The FP64 oracle (numpy, one thread) on a sub-grid of the same
-    workload: 128 x 128 x 8 cells, same materials and cell size."""
+def _oracle_evals(seconds):
+    """Field+torque evaluations of the FP64 oracle (numpy) on a 128x128x8
+    sub-grid of the large-ferromagnet workload (same materials, cell size)
+    for about `seconds`: (evaluations, elapsed s, cells)."""
     import numpy as np
     from inputs import config_c2, random_unit_vectors
     from oracle import dp45
@@ -203,10 +204,51 @@ def cpu_baseline(seconds=15.0):
         el = time.perf_counter() - t0
         if el > seconds:
             break
-    cells = 128 * 128 * 8
-    return {"value": n * cells / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d field+torque evaluations of a 128x128x8 sub-grid of the workload "
-                      "(same materials, cell size), FP64 numpy, %.1f s" % (n, el)}
+    return n, el, 128 * 128 * 8
+
+
+def cpu_worker(seconds):
+    """One oracle process of the all-cores baseline (spawned, one thread)."""
+    return _oracle_evals(seconds)
+
+
+def cpu_model():
+    """The host CPU's model name as lscpu reports it (else the machine type)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def cpu_baseline(seconds=15.0):
+    """The FP64 oracle as it stands (numpy), on the host cores: one process
+    per core (spawned, one thread each: the numpy FFTs and element-wise work
+    of the oracle do not thread), and one thread alone, each on the same
+    128 x 128 x 8 sub-grid of the workload for about `seconds`."""
+    import multiprocessing
+    n1, el1, cells = _oracle_evals(seconds)
+    single = n1 * cells / el1 / 1e6
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    with multiprocessing.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(cpu_worker, [seconds] * cores)
+    total = sum(n * c / el for n, el, c in res) / 1e6
+    evals = sum(n for n, _, _ in res)
+    return {"value": total, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": "%d field+torque evaluations of a 128x128x8 sub-grid of the workload (same materials, "
+                      "cell size), FP64 numpy, %d processes of one thread for %.0f s" % (evals, cores, seconds),
+            "single_thread": {"value": single, "cores": 1,
+                              "sample": "%d evaluations of the same sub-grid in %.1f s" % (n1, el1)}}
 
 
 def run_reference(args):

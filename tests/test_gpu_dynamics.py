@@ -239,6 +239,49 @@ def test_c2_full_size_sampled_parity():
         assert np.abs(got - ref).max() <= bar, ((x, y, z), got, ref)
 
 
+def test_c2_full_size_trajectory_invariants_and_late_parity():
+    """Twenty adaptive Dormand-Prince steps of the large ferromagnet at full
+    size, in the benchmark's launch configuration (a full-size oracle
+    trajectory is hours of numpy): |m| stays 1, the energy does not increase
+    (alpha > 0, no applied field), and B_eff at sampled cells of the evolved
+    state matches the oracle's direct demag sum plus its local terms."""
+    import torch
+    from oracle import demag, fields
+    w = config_c2()
+    p = w.problem
+    nx, ny, nz = p.shape
+    mag = make_magnet(p, w.m0)
+    mag.set_solver(adaptive=True, dt=1e-14, tol=1e-5)
+    e0 = sum(mag.energy().values())
+    mag.step(20)
+    e1 = sum(mag.energy().values())
+    assert mag.time()["steps"] == 20
+    out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    mag.get_m(0, out)
+    m = out.cpu().numpy().astype(np.float64)
+    assert np.abs(np.sqrt((m ** 2).sum(axis=0)) - 1.0).max() <= 1e-5
+    assert e1 <= e0 + 1e-6 * abs(e0), (e0, e1)
+    Bg, _ = gpu_eval(mag, p)
+    mag.close()
+    noct = demag.tensor_octant(p.shape, p.cell)
+    P = fields.cell_params(p)
+    local = sum(fields.effective_fields(
+        p.__class__(p.shape, p.cell, 1, frozenset(p.terms - {"DEMAG"}), p.regions, p.scal, p.vec, p.glob),
+        [m], P=P))
+    rng = np.random.default_rng(4)
+    picks = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (700, 300, 5)]
+    picks += [tuple(int(v) for v in (rng.integers(nx), rng.integers(ny), rng.integers(nz))) for _ in range(13)]
+    cells = [x + nx * (y + ny * z) for x, y, z in picks]
+    Bd = demag.demag_direct(p.shape, p.cell, P["MS"][0] * m, noct=noct, cells=cells)
+    Bo = np.zeros((3, nz, ny, nx))
+    for (x, y, z), bd in zip(picks, Bd.T):
+        Bo[:, z, y, x] = bd + local[:, z, y, x]
+    tol = field_tolerance(p, Bo)
+    for x, y, z in picks:
+        got, ref = Bg[0][:, z, y, x], Bo[:, z, y, x]
+        assert np.all(np.abs(got - ref) <= tol[:, z, y, x]), ((x, y, z), got, ref)
+
+
 @pytest.mark.parametrize("method", ["HEUN", "BS23", "CASHKARP", "RKF45"])
 def test_other_embedded_solvers_match_oracle(method):
     """The other solvers of the paper's table: a fixed-step trajectory and an
