@@ -48,6 +48,33 @@ __device__ __forceinline__ float gradT_at(const float* __restrict__ s, long long
   return acc;
 }
 
+// Bulk rows of G (4th-order central) and of G^T, with the coefficients and
+// the order of the multiply-adds of grad_at / gradT_at, so a bulk cell gets
+// bitwise the same value without the per-term coefficient selection.
+__device__ __forceinline__ float grad_bulk(const float* __restrict__ f, long long cell, long long st, float ih) {
+  const float c = ih * (1.0f / 12.0f);
+  float acc = fmaf(c, f[cell - 2 * st], 0.0f);
+  acc = fmaf(-8.0f * c, f[cell - st], acc);
+  acc = fmaf(8.0f * c, f[cell + st], acc);
+  return fmaf(-c, f[cell + 2 * st], acc);
+}
+__device__ __forceinline__ float gradT_bulk(const float* __restrict__ s, long long cell, long long st, float ih) {
+  const float c = ih * (1.0f / 12.0f);
+  float acc = fmaf(-c, s[cell - 2 * st], 0.0f);
+  acc = fmaf(8.0f * c, s[cell - st], acc);
+  acc = fmaf(-8.0f * c, s[cell + st], acc);
+  return fmaf(c, s[cell + 2 * st], acc);
+}
+// Whether every axis of more than one cell has index i with all the rows the
+// operator needs in the 4th-order bulk: G: 2 <= i <= n - 3; G^T: 4 <= i <= n - 5.
+__device__ __forceinline__ bool in_bulk(const int (&idx)[3], const int (&ext)[3], int margin) {
+  bool b = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (ext[a] > 1) b = b && idx[a] >= margin && idx[a] <= ext[a] - 1 - margin;
+  return b;
+}
+
 __global__ void k_strain(Grid g, ElasticArgs e, int nsub) {
   const long long n = g.n;
   const float* u = e.stage + (long long)3 * nsub * n;
@@ -58,13 +85,23 @@ __global__ void k_strain(Grid g, ElasticArgs e, int nsub) {
     const int idx[3] = {x, y, z}, ext[3] = {g.nx, g.ny, g.nz};
     const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
     float G[3][3], Gv[3][3];
+    if (in_bulk(idx, ext, 2)) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        G[a][j] = grad_at(u + j * n, cell, idx[a], ext[a], st[a], g.ih[a]);
-        Gv[a][j] = e.eta != 0.0f ? grad_at(v + j * n, cell, idx[a], ext[a], st[a], g.ih[a]) : 0.0f;
-      }
+        for (int j = 0; j < 3; ++j) {
+          G[a][j] = ext[a] > 1 ? grad_bulk(u + j * n, cell, st[a], g.ih[a]) : 0.0f;
+          Gv[a][j] = e.eta != 0.0f && ext[a] > 1 ? grad_bulk(v + j * n, cell, st[a], g.ih[a]) : 0.0f;
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          G[a][j] = grad_at(u + j * n, cell, idx[a], ext[a], st[a], g.ih[a]);
+          Gv[a][j] = e.eta != 0.0f ? grad_at(v + j * n, cell, idx[a], ext[a], st[a], g.ih[a]) : 0.0f;
+        }
+    }
     float eps[6] = {G[0][0], G[1][1], G[2][2], 0.5f * (G[0][1] + G[1][0]), 0.5f * (G[0][2] + G[2][0]),
                     0.5f * (G[1][2] + G[2][1])};
     float epv[6] = {Gv[0][0], Gv[1][1], Gv[2][2], 0.5f * (Gv[0][1] + Gv[1][0]), 0.5f * (Gv[0][2] + Gv[2][0]),
@@ -106,11 +143,13 @@ __global__ void k_elastic_rhs(Grid g, ElasticArgs e, Coefs co, int nsub) {
     const int idx[3] = {x, y, z}, ext[3] = {g.nx, g.ny, g.nz};
     const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
     float f[3] = {0.0f, 0.0f, 0.0f};
+    const bool bulkT = in_bulk(idx, ext, 4), bulk = in_bulk(idx, ext, 2);
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        f[b] -= gradT_at(e.sig + sidx[a][b] * n, cell, idx[a], ext[a], st[a], g.ih[a]);
+        f[b] -= bulkT ? (ext[a] > 1 ? gradT_bulk(e.sig + sidx[a][b] * n, cell, st[a], g.ih[a]) : 0.0f)
+                      : gradT_at(e.sig + sidx[a][b] * n, cell, idx[a], ext[a], st[a], g.ih[a]);
     if (e.terms & 64u) {
       int reg = UNI ? 0 : co.regions[cell];
       for (int s = 0; s < nsub; ++s) {
@@ -120,7 +159,9 @@ __global__ void k_elastic_rhs(Grid g, ElasticArgs e, Coefs co, int nsub) {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int j = 0; j < 3; ++j) G[a][j] = grad_at(m + j * n, cell, idx[a], ext[a], st[a], g.ih[a]);
+          for (int j = 0; j < 3; ++j)
+            G[a][j] = bulk ? (ext[a] > 1 ? grad_bulk(m + j * n, cell, st[a], g.ih[a]) : 0.0f)
+                           : grad_at(m + j * n, cell, idx[a], ext[a], st[a], g.ih[a]);
         float mx = m[cell], my = m[n + cell], mz = m[2 * n + cell];
         float B1 = R.b1, B2 = R.b2;
         f[0] += 2.0f * B1 * mx * G[0][0] + B2 * (mx * (G[1][1] + G[2][2]) + my * G[1][0] + mz * G[2][0]);
