@@ -22,8 +22,10 @@ Every function follows a passage of the paper (arXiv 2411.18194, "Methods"):
                 adaptive step-size controller.
 
 Parity pinned or unpinned: see the pins in tests/test_oracle_*.py.  The
-adaptive-controller constants and the elastic edge stencils are readings
-of passages the paper leaves open; they are agreed between the oracle and
-the CUDA path by construction only ("parity unpinned" beyond consistency
-and stability checks).
+adaptive-controller constants are a reading of a passage the paper leaves
+open; they are agreed between the oracle and the CUDA path by construction
+only ("parity unpinned").  The elastic edge stencils, also a reading, are
+pinned by the exactness every row must have (linear and quadratic fields,
+quartics in the bulk), the adjointness of the divergence, the absence of
+growing modes and energy conservation.
 """

@@ -145,3 +145,29 @@ def test_energy_conserved_without_viscosity():
     st = o.run_fixed(st, 2e-14, 100)
     E1 = sum(elastic.elastic_energy(p, st.u, st.v))
     assert abs(E1 / E0 - 1) < 1e-9
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 9, 17])
+def test_gradient_rows_exact_on_polynomials(n):
+    """Every row of the gradient scheme is a consistent derivative of the
+    order its stencil has, which fixes its coefficients: all rows (one-sided
+    edges, second-order central next to them, fourth-order bulk) differentiate
+    linear fields exactly, every row but those of n = 2 quadratics, and the
+    bulk rows quartics too (n >= 5).  A wrong coefficient or a dropped term in
+    any row fails one of these."""
+    h = 1.5
+    x = np.arange(n, dtype=np.float64) * h + 0.7
+
+    def d(f):
+        return elastic.d1(f[None, None, :], -1, h)[0, 0]
+    assert np.allclose(d(3.0 - 2.0 * x), -2.0, rtol=0, atol=1e-12)
+    if n >= 3:
+        assert np.allclose(d(1.0 + 0.5 * x - 0.25 * x ** 2), 0.5 - 0.5 * x, rtol=0, atol=1e-11)
+    if n >= 5:
+        bulk = slice(2, n - 2)
+        for p in (3, 4):
+            f, df = x ** p, p * x ** (p - 1)
+            assert np.allclose(d(f)[bulk], df[bulk], rtol=1e-12, atol=1e-9), p
+        # and the bulk rows are not exact at degree 5 (the stencil is 4th order, not higher)
+        f5 = x ** 5
+        assert np.abs(d(f5)[bulk] - 5 * x[bulk] ** 4).max() > 1e-6
